@@ -1,0 +1,166 @@
+"""Tweak, greedy directions and the reduction policies (oracle; test infrastructure only).
+
+Sec. 3.1 Algorithm 1 (Tweak), Sec. 4 Algorithm 3 (greedy v), the abstract
+reduction game of Sec. 3.4 and the three policies of Sec. 4.1-4.3.
+Exponent vectors are tuples in N^{n+1}.  A term of pole order K has
+|u| = n + d (K - n) (its numerator is x^u g / x^S with g in Homog_{dn-n}).
+"""
+
+
+def tweak(I, m):
+    """Algorithm 1: remove m units from the front of I (lowest index first).
+
+    Returns (I', J) with I = I' + J and |J| = min(m, |I|).
+    """
+    out = list(I)
+    J = [0] * len(I)
+    left = m
+    for i in range(len(out)):
+        if left == 0:
+            break
+        take = min(out[i], left)
+        out[i] -= take
+        J[i] += take
+        left -= take
+    return tuple(out), tuple(J)
+
+
+def greedy_v(d, u, S):
+    """Algorithm 3: v with |v| = d and v <= u, v_s >= 1 for s in S with u_s != 0.
+
+    Readings of the printed algorithm: S is scanned in ascending order, the
+    count i is tested before every increment of the round-robin loop, and
+    the vector built (v) is what is returned.
+    """
+    v = [0] * len(u)
+    i = d
+    for s in sorted(S):
+        if u[s] != 0:
+            v[s] = 1
+            i -= 1
+            if i == 0:
+                break
+    while i > 0:
+        progressed = False
+        for m in range(len(u)):
+            if i > 0 and v[m] < u[m]:
+                v[m] += 1
+                i -= 1
+                progressed = True
+        if not progressed:
+            raise ValueError("|u| < d: no direction")
+    return tuple(v)
+
+
+def in_V_full(u, v, k, S):
+    """v in V_S(u, k) intersected with V_full: |v| = d implied by caller.
+
+    u - k v >= 0, and for i in S: u_i != 0 implies v_i != 0 (the condition
+    of Prop. 3.3 on the exponent before the step).
+    """
+    for i in range(len(u)):
+        if u[i] - k * v[i] < 0:
+            return False
+        if i in S and u[i] != 0 and v[i] == 0:
+            return False
+    return True
+
+
+def k_max(u, v, n, d):
+    """Largest k with u - k v >= 0 and |u - k v| >= n (Sec. 4.2)."""
+    k = (sum(u) - n) // d
+    for i in range(len(u)):
+        if v[i] > 0:
+            k = min(k, u[i] // v[i])
+    return k
+
+
+def pole_order(u, n, d):
+    return (sum(u) - n) // d + n
+
+
+def sub_kv(u, v, k):
+    return tuple(a - k * b for a, b in zip(u, v))
+
+
+class GameLog:
+    """Cost bookkeeping of the reduction game (Sec. 3.4): M k + S per chunk, D per duplicate."""
+
+    def __init__(self):
+        self.chunks = 0
+        self.steps = 0          # sum of k over chunks (one per term per pole order)
+        self.column_steps = 0   # steps times the number of live columns of the term
+        self.merges = 0         # duplicates removed
+
+    def cost(self, cM, cS, cD):
+        return cM * self.steps + cS * self.chunks + cD * self.merges
+
+
+def merge_terms(terms, add, log):
+    """Move 2: combine terms with equal u.  terms: list of (u, payload)."""
+    out = {}
+    order = []
+    for u, w in terms:
+        if u in out:
+            out[u] = add(out[u], w)
+            log.merges += 1
+        else:
+            out[u] = w
+            order.append(u)
+    return [(u, out[u]) for u in order]
+
+
+def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
+    """Run a policy on the initial term list; returns the terms at |u| = n.
+
+    reduce_chunk(u, v, k, payload) -> payload after k steps in direction v.
+    add(a, b) -> merged payload.
+    """
+    S = set(S)
+    if policy == "depth_first":
+        out = []
+        for u, w in terms:
+            while sum(u) > n:
+                v = greedy_v(d, u, S)
+                k = k_max(u, v, n, d)
+                assert k >= 1 and in_V_full(u, v, k, S)
+                w = reduce_chunk(u, v, k, w)
+                u = sub_kv(u, v, k)
+            out.append((u, w))
+        return out
+    if policy == "p_chunk":
+        live = merge_terms(terms, add, log)
+        done = []
+        while live:
+            L = max(sum(u) for u, _ in live)
+            nxt = []
+            for u, w in live:
+                if sum(u) == L:
+                    v = greedy_v(d, u, S)
+                    K = pole_order(u, n, d)
+                    k = min(p, K - n, k_max(u, v, n, d))
+                    assert k >= 1 and in_V_full(u, v, k, S)
+                    w = reduce_chunk(u, v, k, w)
+                    u = sub_kv(u, v, k)
+                nxt.append((u, w))
+            nxt = merge_terms(nxt, add, log)
+            done += [(u, w) for u, w in nxt if sum(u) == n]
+            live = [(u, w) for u, w in nxt if sum(u) > n]
+        return done
+    if policy == "var_by_var":
+        live = merge_terms(terms, add, log)
+        for t in range(n, -1, -1):
+            nxt = []
+            for u, w in live:
+                while sum(u) > n and u[t] > 0:
+                    v = greedy_v(d, u, S)
+                    k = k_max(u, v, n, d)
+                    assert k >= 1 and in_V_full(u, v, k, S)
+                    w = reduce_chunk(u, v, k, w)
+                    u = sub_kv(u, v, k)
+                nxt.append((u, w))
+            live = merge_terms(nxt, add, log)
+        # after the u_0 phase every term has |u| = n
+        assert all(sum(u) == n for u, _ in live)
+        return live
+    raise ValueError("unknown policy %r" % policy)
