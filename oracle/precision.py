@@ -3,13 +3,17 @@
 Sec. 2.5.  The paper delegates r_m to a lemma of another paper and N_m to an
 algorithm of another paper, neither printed.  The readings used here:
 
-* r (used as r_m for every m): the coefficients a_i of P(T), i <= b/2,
-  satisfy |a_i| <= C(b, i) p^{(n-1) i / 2} (Weil).  If the column-scaled
-  Frobenius matrix C (F = C diag(p^{n-m})) is known mod p^r, then a_i is
-  known mod p^{r + H(i)}, H the Hodge polygon (slopes n - m, Mazur's Newton
-  over Hodge), because every principal i-minor of F carries at least
-  p^{H(i)}.  So r = max_i (e_i - H(i)) with e_i the least e such that
-  p^e > 2 C(b, i) p^{(n-1) i / 2}.
+* r_m (the relative precision of the columns of pole order m): the
+  coefficients a_i of P(T), i <= b/2, satisfy |a_i| <= C(b, i) p^{(n-1)i/2}
+  (Weil), so a_i is fixed by its residue mod p^{e_i}, e_i the least e with
+  p^e > 2 C(b, i) p^{(n-1) i / 2}.  Write F = C diag(p^{sigma_j}) with
+  sigma_j = n - m_j (Mazur's Newton over Hodge: C is integral).  If the
+  columns of C of pole order m are known mod p^{r_m}, a principal minor of
+  F on a column set I is known mod p^{sum_{j in I} sigma_j + min_{j in I}
+  r_{m_j}}.  So it suffices that r_m >= e_i - G_m(i) for every i <= b/2,
+  where G_m(i) = (n - m) + the sum of the i - 1 smallest slopes of the
+  other columns: r_m = max(1, max_i (e_i - G_m(i))).  The paper states that
+  r_m depends on m and p; this is the reading of how.
 * N_m: the truncation error of Prop. 2.1 at N terms is a sum of integral
   forms of pole order p(m + i), i >= N, multiplied by p^{m-1+i}.  Reducing
   such a form to the basis costs at most LOSS(K) digits (a logarithmic bound
@@ -62,12 +66,25 @@ def weil_digits(n, b, p, i):
     return e
 
 
-def relative_precision(n, p, pole_orders):
+def coefficient_digits(n, p, b):
+    """[e_0, ..., e_{b//2}]: a_i is determined by a_i mod p^{e_i}."""
+    return [weil_digits(n, b, p, i) for i in range(b // 2 + 1)]
+
+
+def relative_precisions(n, p, pole_orders):
+    """{m: r_m} for the pole orders present (see the module docstring)."""
     b = len(pole_orders)
-    H = hodge_polygon(n, pole_orders)
-    r = 1
-    for i in range(0, b // 2 + 1):
-        r = max(r, weil_digits(n, b, p, i) - H[i])
+    e = coefficient_digits(n, p, b)
+    slopes = sorted(n - m for m in pole_orders)
+    r = {}
+    for m in sorted(set(pole_orders)):
+        others = list(slopes)
+        others.remove(n - m)
+        best = 1
+        for i in range(1, b // 2 + 1):
+            G = (n - m) + sum(others[:i - 1])
+            best = max(best, e[i] - G)
+        r[m] = best
     return r
 
 
@@ -110,16 +127,22 @@ def series_order(m, r, n, p):
 class Precision:
     def __init__(self, n, d, p, pole_orders, r=None, N=None):
         """pole_orders: pole order m of each basis element.  r, N: optional overrides
-        (N a dict m -> N_m or an int for all m) used by small parity cases."""
+        (an int for all m, or a dict m -> value) used by small parity cases."""
         self.n, self.d, self.p = n, d, p
         ms = sorted(set(pole_orders))
-        self.r = relative_precision(n, p, pole_orders) if r is None else r
+        self.e = coefficient_digits(n, p, len(pole_orders))
+        if r is None:
+            self.r = relative_precisions(n, p, pole_orders)
+        elif isinstance(r, int):
+            self.r = {m: r for m in ms}
+        else:
+            self.r = dict(r)
         if N is None:
-            self.N = {m: series_order(m, self.r, n, p) for m in ms}
+            self.N = {m: series_order(m, self.r[m], n, p) for m in ms}
         elif isinstance(N, int):
             self.N = {m: N for m in ms}
         else:
             self.N = dict(N)
         self.s = {m: self.N[m] + m - 1 for m in ms}
-        self.M = max(self.r + vp_factorial(p * self.s[m] - 1, p) - m + 1 for m in ms)
+        self.M = max(self.r[m] + vp_factorial(p * self.s[m] - 1, p) - m + 1 for m in ms)
         self.q = p ** self.M

@@ -152,7 +152,7 @@ def frobenius_terms(X, basis, prec):
 
 
 def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
-                 column_order=None, use_c=True, want_P=True):
+                 column_order=None, use_c=True, want_P=True, normalise=True):
     """Run the whole computation.  Returns a ZetaResult with
     basis, prec (r, N_m, M, q), Y (unnormalised b x b mod q), C (columns of
     p^{m-n-1} sigma mod p^r), F (= C diag(p^{n-m})), P (list a_0..a_b) and
@@ -221,12 +221,16 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
                     H[col][e] = (H[col].get(e, 0) + a) % q
     for col in range(b):
         Y[:, col] = fin.reduce(H[col])
+    if not normalise:
+        res = ZetaResult()
+        res.n, res.d, res.p, res.coeffs = n, d, p, list(coeffs)
+        res.basis, res.prec, res.Y, res.log, res.policy = basis, prec, Y, log, policy
+        return res
 
-    # Step 7: normalisation.  Y = ((p s_m - 1)!/(n-1)!) p^{1-m} c.
-    r = prec.r
-    pr = p ** r
+    # Step 7: normalisation.  Y = ((p s_m - 1)!/(n-1)!) p^{1-m} c, c known mod p^{r_m}.
     C = np.zeros((b, b), dtype=object)
     for col, (m, beta) in enumerate(basis):
+        pr = p ** prec.r[m]
         sm = prec.s[m]
         v = vp_factorial(p * sm - 1, p)
         e = v - m + 1
@@ -250,35 +254,36 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
     res.basis, res.prec, res.Y, res.C, res.F, res.log = basis, prec, Y, C, F, log
     res.policy = policy
     if want_P:
-        res.P, res.eps = charpoly_lift(n, p, F, C, pole_orders, r)
+        res.P, res.eps = charpoly_lift(n, p, F, C, pole_orders, prec)
     return res
 
 
-def charpoly_lift(n, p, F, C, pole_orders, r):
+def charpoly_lift(n, p, F, C, pole_orders, prec):
     """P(T) = det(1 - T F) in Z[T] (Sec. 2.1) from F known to the stated precision.
 
-    a_i for i <= b/2 is known mod p^{r + H(i)} and lifted to the symmetric
-    range; the rest follows from the functional equation
+    With the columns of pole order m known mod p^{r_m + n - m}, a_i for
+    i <= b/2 is known mod p^{e_i} (oracle.precision) and lifted to the
+    symmetric range; the rest follows from the functional equation
     a_{b-i} = eps p^{w(b/2 - i)} a_i, w = n - 1, with
     eps = (-1)^b det(C) (a_b = (-1)^b det F and det F = det(C) p^{H(b)}).
     """
     b = len(pole_orders)
     w = n - 1
-    H = hodge_polygon(n, pole_orders)
     cp = berkowitz_charpoly(F.tolist())   # det(T I - F) = sum cp[i] T^{b-i}; a_i = cp[i]
     a = [0] * (b + 1)
     a[0] = 1
     for i in range(1, b // 2 + 1):
-        mod = p ** (r + H[i])
+        mod = p ** prec.e[i]
         x = cp[i] % mod
         if x > mod // 2:
             x -= mod
         a[i] = x
+    rmin = min(prec.r.values())
     detC = berkowitz_charpoly(C.tolist())[b] * (-1) ** b   # det(C)
-    sgn = ((-1) ** b * detC) % (p ** r)
+    sgn = ((-1) ** b * detC) % (p ** rmin)
     if sgn == 1:
         eps = 1
-    elif sgn == p ** r - 1:
+    elif sgn == p ** rmin - 1:
         eps = -1
     else:
         raise ArithmeticError("det(C) is not +-1 mod p^r: %d" % sgn)

@@ -22,7 +22,8 @@ def main():
         fh.write("# P(T) is also fixed by #X(F_11^r), r = 1..3 (tests/test_oracle_zeta.py)\n")
         fh.write("n d p: %d %d %d\n" % (n, d, p))
         fh.write("coeffs: %s\n" % " ".join(map(str, c)))
-        fh.write("r N M: %d %s %d\n" % (res.prec.r, " ".join("%d=%d" % kv for kv in sorted(res.prec.N.items())), res.prec.M))
+        fh.write("r_m N_m M: %s %s %d\n" % (" ".join("r%d=%d" % kv for kv in sorted(res.prec.r.items())),
+                                          " ".join("N%d=%d" % kv for kv in sorted(res.prec.N.items())), res.prec.M))
         fh.write("P: %s\n" % " ".join(map(str, res.P)))
 
 

@@ -177,8 +177,15 @@ def test_precision_rules():
     for p in [7, 11]:
         for x in [1, 6, 7, 48, 49, 50, 120]:
             assert precision.vp_factorial(x, p) == (precision.vp(factorial(x), p) if x > 0 else 0)
-    # genus 3 over F_11: a_3 <= 20 * 11^1.5 ~ 730, 2*730 < 11^4, Hodge polygon 0 up to i = 3
-    assert precision.relative_precision(2, 11, [1, 1, 1, 2, 2, 2]) == 4
+    # genus 3 over F_11: a_3 <= 20 * 11^1.5 ~ 730, 2*730 < 11^4; columns of pole order 1
+    # carry a factor p in every minor they enter, so they need one digit less
+    assert precision.coefficient_digits(2, 11, 6) == [1, 2, 3, 4]
+    assert precision.relative_precisions(2, 11, [1, 1, 1, 2, 2, 2]) == {1: 3, 2: 4}
+    # genus 6 over F_41: 2 * C(12,6) * 41^3 > 41^5, so e_6 = 6 and r_2 = 6, r_1 = 5
+    assert precision.relative_precisions(2, 41, [1] * 6 + [2] * 6) == {1: 5, 2: 6}
+    # K3 (Hodge slopes 2, 1 x 19, 0) over F_7
+    pr = precision.Precision(3, 4, 7, [1] + [2] * 19 + [3])
+    assert pr.r[3] >= pr.r[2] >= pr.r[1] >= 1
     # series orders reproduce the smallest stable N found for plane curves
     assert precision.series_order(1, 4, 2, 11) == 5
     assert precision.series_order(2, 4, 2, 11) == 4

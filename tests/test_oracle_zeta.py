@@ -95,8 +95,9 @@ def _weil_checks(res):
     from oracle.algebra import berkowitz_charpoly
     cp = berkowitz_charpoly(res.F.tolist())
     H = hodge_polygon(n, pole)
+    rmin = min(res.prec.r.values())
     for j in range(b // 2 + 1, b + 1):
-        mod = p ** (res.prec.r + H[j])
+        mod = p ** (rmin + H[j])
         assert (cp[j] - P[j]) % mod == 0
 
 
@@ -127,8 +128,8 @@ def test_precision_is_stable_under_more_terms(quartic_f11):
     (n, d, p, c), ref = quartic_f11
     N = {m: k + 1 for m, k in ref.prec.N.items()}
     res = zeta.compute_zeta(n, d, p, c, N=N, r=ref.prec.r)
-    r = ref.prec.r
-    assert ((res.C - ref.C) % p ** r == 0).all()
+    for col, (m, _) in enumerate(ref.basis):
+        assert ((res.C[:, col] - ref.C[:, col]) % p ** ref.prec.r[m] == 0).all()
     assert res.P == ref.P
 
 
