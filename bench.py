@@ -1,0 +1,292 @@
+"""Benchmark: zeta functions of a batch of smooth plane quintics on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--policy depth_first] [--path vector]
+
+A step is one pass of the whole hot path over one batch: every reduction
+chain of every instance run to pole order n by the recurrence kernel, then
+the per-instance sums.  `value` is zeta functions per second with the
+inputs (start terms, sections, tables: larger than L2) resident in HBM;
+`e2e` is the same metric through zeta_batch with host buffers (host setup,
+uploads, kernels, download and host finish all inside the timed region).
+Under torchrun every rank runs its own batch of the same size (weak
+scaling, no collective on the data path).  `--impl reference` times the
+CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import zeta_inputs as zi  # noqa: E402
+
+METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
+WORKLOAD = "quintic_curves"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _instances(rank, count):
+    """Instances rank*count .. rank*count+count-1 of the quintic-curve workload."""
+    from oracle.cohomology import is_smooth  # the oracle's smoothness predicate only filters
+    out = []
+    for i in range(rank * count, rank * count + count):
+        n, d, p, c, _ = zi.draw_instance(WORKLOAD, i, is_smooth)
+        out.append((n, d, p, c))
+    return out
+
+
+def _instances_lib(rank, count, z):
+    """Same instances, accepted by the library's own smoothness test."""
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c))
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    return [zi.draw_instance(WORKLOAD, i, accept)[:4] for i in range(rank * count, rank * count + count)]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_one(spec):
+    from oracle import zeta as oz
+    n, d, p, c = spec
+    t = time.perf_counter()
+    res = oz.compute_zeta(n, d, p, c)
+    return time.perf_counter() - t, res.log.column_steps, res.P
+
+
+def oracle_sample(specs, cores):
+    """Time the oracle on `specs` with one process per instance over `cores` processes."""
+    from oracle import zeta as oz
+    oz.build_helper()
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_one, specs)
+    wall = time.perf_counter() - t0
+    return wall, res
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    sample_n = max(1, min(cores, 16))
+    specs = _instances(0, sample_n)
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    walls = []
+    steps = 0
+    for _ in range(max(1, args.steps)):
+        wall, res = oracle_sample(specs, cores)
+        walls.append(wall)
+        steps = sum(r[1] for r in res)
+    wall = statistics.median(walls)
+    value = sample_n / wall
+    sample = "first %d instances of %s (primes %s), %d processes, oracle as it stands" % (
+        sample_n, WORKLOAD, sorted(set(s[2] for s in specs)), min(cores, sample_n))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "zeta/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int (exact big integers)", "data": "synthetic",
+        "steps_per_s": steps / wall,
+        "config": {"workload": "quintic_curves_4096", "sample": sample_n},
+        "cpu_baseline": {"value": value, "unit": "zeta/s", "cores": min(cores, sample_n), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "zeta/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--policy", default="depth_first")
+    ap.add_argument("--path", default="vector")
+    ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2602_24155_gb300 as z
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.current_stream()
+    ctx = z.zeta_create(local, stream.cuda_stream)
+    specs = _instances_lib(rank, args.count, z)
+    opt = dict(policy=args.policy, path=args.path)
+
+    # device-resident inputs: prepare once, then time the kernels
+    plan = z.zeta_batch_prepare(ctx, specs, **opt)
+    for _ in range(args.warmup):
+        plan.run()
+    torch.cuda.synchronize()
+    P_warm, per, tot_warm = plan.finish()
+    assert all(P is not None for P in P_warm), "an instance failed"
+
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    P_timed, _, tot = plan.finish()   # kernel-event timing of the timed launches
+    assert P_timed == P_warm
+    plan.release()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    ms_per_step = ms_max / args.steps
+    total_instances = args.count * world
+    value = total_instances / (ms_per_step / 1000.0)
+    column_steps = tot["column_steps"] * world
+    s = per[0]["s"]
+
+    # end to end through the C ABI with host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P_e2e, per_e2e, tot_e2e = z.zeta_batch(ctx, specs, **opt)
+    e2e_s = time.perf_counter() - t0
+    assert P_e2e == P_warm
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = total_instances / float(e2e_t.item())
+    coeff_bytes = sum(4 * len(sp[3]) for sp in specs)
+
+    # roofline of the recurrence kernel: modular multiply-adds (s^2 per column step)
+    peaks = _peaks()
+    ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
+    macs_per_launch = tot["column_steps"] * s * s
+    achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # ALU peak: 152 SMs x 64 32-bit IMAD per clock / 4 IMAD.WIDE per modular MAC (30-bit limbs)
+    alu_peak = 152 * 64 / 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "zeta/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "steps_per_s": column_steps / (ms_per_step / 1000.0),
+        "config": {"workload": "quintic_curves_4096", "n": 2, "d": 5, "count_per_gpu": args.count,
+                   "primes": list(zi.PRIMES_QUINTIC_CURVES), "policy": args.policy, "path": args.path,
+                   "l2": "inputs larger than L2 (%.2f GB resident)" % (tot["bytes_h2d"] / 1e9),
+                   "column_steps_per_step": column_steps},
+        "e2e": {"value": e2e_value, "unit": "zeta/s", "h2d_bytes_per_step": coeff_bytes + tot_e2e["bytes_h2d"],
+                "d2h_bytes_per_step": tot_e2e["bytes_d2h"] + 16 * sum(len(P) for P in P_e2e)},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "k_depth_first", "ms_per_launch": ms_kernel,
+                     "peak_basis": "152 SM x 64 IMAD/clk / 4 IMAD.WIDE per 30-bit-limb modular MAC at %.0f MHz"
+                                   % peaks.get("sm_max_mhz", 2070.0)},
+        "clocks": clk,
+        "host": {"ms_setup": tot_e2e["ms_host_setup"], "ms_finish": tot_e2e["ms_host_finish"],
+                 "e2e_s": e2e_s},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample_n = max(1, min(cores, 16))
+        wall, res = oracle_sample(specs[:sample_n], cores)
+        for (P_o, (_, _, P_ref)) in zip(P_warm[:sample_n], res):
+            assert P_o == P_ref, "GPU result differs from the oracle"
+        line["cpu_baseline"] = {"value": sample_n / wall, "unit": "zeta/s", "cores": min(cores, sample_n),
+                                "kind": "oracle",
+                                "sample": "first %d instances (all %d primes cycle), one process each; "
+                                          "results also checked equal to the GPU's" % (sample_n, min(sample_n, 12))}
+    if rank == 0:
+        print(json.dumps(line))
+    z.zeta_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * zeta.h -- C ABI of the GB300 controlled-reduction library.
+ *
+ * Computes the zeta function of a smooth projective hypersurface
+ * X = V(f) in P^n over F_p (7 <= p < 50) by controlled reduction in p-adic
+ * cohomology (arXiv 2602.24155): (f, p, precision, policy) -> matrix of
+ * p^{-1} sigma on H^n_dR(U) -> P(T) = det(1 - T F) in Z[T], with
+ * Z(X, T) = P(T)^{(-1)^n} / prod_{i<n} (1 - p^i T)   (paper Sec. 2.1).
+ *
+ * The long linear recurrence w <- M(y) w mod p^M with M(y) = y A + B
+ * (Sec. 3.2, Algorithm 2), driven by a reduction policy (Sec. 4), runs in
+ * CUDA kernels for sm_103a; host code in this library prepares the start
+ * vectors (Prop. 2.1, Algorithm 1) and finishes with the final
+ * Griffiths-Dwork reduction (Sec. 3.3 step (2)) and the characteristic
+ * polynomial.  There is no CPU fallback: every entry point that needs the
+ * GPU returns ZETA_ERR_DEVICE when no CUDA device is usable.
+ *
+ * Conventions common to all entry points
+ *  - No exceptions cross the ABI; every call returns a zeta_status.
+ *  - The caller owns every buffer it passes; the library never frees them.
+ *    The context owns its device memory and releases it in zeta_destroy.
+ *  - Coefficients of f: C(n+d, n) values in [0, p), monomials of degree d in
+ *    n+1 variables in descending lexicographic order of the exponent vector
+ *    (x_0 first; for n = 2, d = 2: x0^2, x0x1, x0x2, x1^2, x1x2, x2^2).
+ *  - The basis of H^n_dR(U) is the monomial basis of Sec. 2.3: for
+ *    m = 1..n the monomials of degree dm-n-1 that are not pivot columns of
+ *    the row echelon form over F_p of the image of the Jacobian map M_k
+ *    (columns in the order above).  Basis order: m ascending, then monomial
+ *    order.  b = dim = ((d-1)^{n+1} + (-1)^{n+1}(d-1)) / d.
+ *  - Supported: S = {0..n} controlled reduction (Prop. 3.3), which needs
+ *    d >= n+1; p^M < 2^63.  Other inputs return ZETA_ERR_UNSUPPORTED or
+ *    ZETA_ERR_PRECISION.
+ *  - Calls are synchronous: they return after the device work has finished.
+ *    One context must not be used from two host threads at once.
+ */
+#ifndef ZETA_H
+#define ZETA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZETA_OK = 0,
+    ZETA_ERR_ARG = 1,          /* null pointer, bad size, coefficient out of range */
+    ZETA_ERR_NOT_SMOOTH = 2,   /* the Jacobian criterion fails (Sec. 2.1, Def. 3.1) */
+    ZETA_ERR_UNSUPPORTED = 3,  /* p < 7, p >= 50, p | d, p <= n, or d < n+1 */
+    ZETA_ERR_PRECISION = 4,    /* p^M would not fit below 2^63 */
+    ZETA_ERR_DEVICE = 5,       /* CUDA error or no usable device */
+    ZETA_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+    ZETA_ERR_OOM = 7,          /* host or device allocation failed */
+    ZETA_ERR_INTERNAL = 8      /* an internal consistency check failed */
+} zeta_status;
+
+/* Reduction policies (Sec. 4).  Every policy yields the same result. */
+typedef enum {
+    ZETA_POLICY_PCHUNK = 0,      /* Sec. 4.1: chunks of p on the terms of largest norm, then merge */
+    ZETA_POLICY_DEPTH_FIRST = 1, /* Sec. 4.2: greedy v, largest chunk, never merge */
+    ZETA_POLICY_VAR_BY_VAR = 2   /* Sec. 4.3: clear u_n, merge, clear u_{n-1}, ... */
+} zeta_policy;
+
+/* Which kernel runs the recurrence. */
+typedef enum {
+    ZETA_PATH_VECTOR = 0,  /* modular matrix-vector steps on the CUDA cores */
+    ZETA_PATH_GEMM = 1     /* exact limb-split modular GEMM steps on the tensor cores */
+} zeta_path;
+
+typedef struct {
+    uint32_t n, d, p;           /* X in P^n of degree d over F_p */
+    const uint32_t *coeffs;     /* host pointer, C(n+d, n) values in [0, p) */
+} zeta_hypersurface;
+
+typedef struct {
+    zeta_policy policy;
+    zeta_path path;
+    /* Precision overrides (0 = the rules of Sec. 2.5 as read in the
+     * library's documentation).  r_override sets the relative precision r;
+     * N_override[m-1] sets the series order N_m.  With overrides smaller
+     * than the rules the Frobenius matrix is a truncation and P(T) is not
+     * the zeta function; used for small parity cases. */
+    uint32_t r_override;
+    uint32_t N_override[8];
+    uint32_t flags;             /* ZETA_FLAG_* bits */
+} zeta_options;
+
+/* Stop after the unnormalised columns Y (no division by p^(v-m+1), no
+ * charpoly): for truncated precisions whose Y is not divisible. */
+#define ZETA_FLAG_Y_ONLY 1u
+
+typedef struct {
+    int32_t status;          /* per-instance status (zeta_batch) */
+    uint32_t b;              /* dim H^n_dR(U) = deg P */
+    uint32_t r;              /* max_m r_m: relative precision of the Frobenius columns */
+    uint32_t M;              /* algorithm precision: arithmetic mod p^M */
+    uint32_t N[8];           /* series orders N_m, m = 1..n */
+    uint32_t s;              /* side of the step matrices, C(dn, n) */
+    int32_t eps;             /* sign of the functional equation */
+    uint64_t chains;         /* distinct start exponents u after combining terms */
+    uint64_t terms;          /* nonzero terms of the Frobenius expansion */
+    uint64_t chunks;         /* chunks played (Sec. 3.4 move 1) */
+    uint64_t steps;          /* reduction steps: sum of chunk lengths over chains */
+    uint64_t column_steps;   /* steps times live columns: one length-s vector advanced one pole order */
+    double ms_host_setup;    /* host: basis, section, expansion */
+    double ms_device;        /* device: upload + recurrence + download */
+    double ms_host_finish;   /* host: final reduction map, normalisation, charpoly */
+    double ms_kernel;        /* device time of the recurrence kernel (CUDA events), summed over launches */
+    uint64_t kernel_launches;/* launches of the recurrence kernel covered by ms_kernel */
+    uint64_t bytes_h2d;      /* bytes copied host -> device (start terms, sections, tables) */
+    uint64_t bytes_d2h;      /* bytes copied device -> host (numerators) */
+} zeta_stats;
+
+typedef struct zeta_ctx zeta_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL for the legacy default stream; may come from torch).  The
+ * context allocates device memory lazily and keeps it for reuse. */
+zeta_status zeta_create(zeta_ctx **out, int device, void *cuda_stream);
+
+/* Release every device and host resource of the context.  NULL is allowed. */
+zeta_status zeta_destroy(zeta_ctx *ctx);
+
+/* Human-readable text of the last error of this context (never NULL). */
+const char *zeta_last_error(const zeta_ctx *ctx);
+
+/* Sizes of an instance without running it (host only, no device needed):
+ * b = deg P, r, M (Sec. 2.5), s = C(dn, n).  Any output pointer may be NULL.
+ * Returns ZETA_ERR_NOT_SMOOTH for a singular f. */
+zeta_status zeta_query(const zeta_hypersurface *hs, const zeta_options *opt,
+                       uint32_t *b, uint32_t *r, uint32_t *M, uint32_t *s);
+
+/* Frobenius matrix of one hypersurface.
+ *  F_out: caller-owned host buffer of b*b uint64, row-major: column j is
+ *         p^{-1} sigma applied to basis element j, in the basis above.
+ *         Column j (pole order m) is exact mod p^{r_m + n - m}; entries are
+ *         reduced to [0, p^{r_m+n-m}).  r_m (Sec. 2.5) is the least relative
+ *         precision of the pole-order-m columns for which every a_i,
+ *         i <= b/2, is fixed: r_m = max(1, max_i e_i - G_m(i)) with e_i the
+ *         least e with p^e > 2 C(b,i) p^{(n-1)i/2} and G_m(i) = (n - m) + the
+ *         i-1 smallest slopes n - m' of the other basis elements.
+ *  Y_out: optional (may be NULL) b*b uint64: the unnormalised columns
+ *         ((p s_m - 1)! / (n-1)!) p^{1-m} sigma-coordinates mod p^M before
+ *         the exact division (a library-independent quantity: it does not
+ *         depend on the policy or the kernel path).
+ *  st:    optional statistics. */
+zeta_status zeta_frobenius(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt,
+                           uint64_t *F_out, uint64_t *Y_out, zeta_stats *st);
+
+/* P(T) = det(1 - T F) in Z[T] of one hypersurface (Sec. 2.1; coefficients
+ * a_i for i <= b/2 from F, the rest from the functional equation
+ * a_{b-i} = eps p^{(n-1)(b-2i)/2} a_i).
+ * P_out: caller-owned 2*(b+1) int64: coefficient i is the 128-bit two's
+ * complement integer with low word P_out[2i] (read as unsigned) and high
+ * word P_out[2i+1]; a_0 = 1. */
+zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt,
+                          int64_t *P_out, zeta_stats *st);
+
+/* Many hypersurfaces (any mix of n, d, p) in one device pass.
+ *  P_out: count * stride * 2 int64; instance i writes b_i+1 coefficients
+ *         (two words each, as in zeta_charpoly) at P_out + 2*i*stride
+ *         (stride >= max b_i + 1).
+ *  per_instance: optional count zeta_stats; status of each instance in
+ *         .status (the call returns ZETA_OK if the batch ran, even when some
+ *         instances were rejected).
+ *  total: optional aggregate statistics. */
+zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
+                       const zeta_options *opt, int64_t *P_out, size_t stride,
+                       zeta_stats *per_instance, zeta_stats *total);
+
+/* The batch in phases, so that the device part can be timed on its own.
+ *  zeta_batch_prepare: host setup of every instance (thread pool) and upload
+ *      of the start terms, sections and tables to device memory.  The plan
+ *      owns that device memory until zeta_batch_release.
+ *  zeta_batch_run: enqueue the recurrence kernels on the context's stream
+ *      and return without waiting (inputs already resident).  May be called
+ *      again on the same plan; each run recomputes the same numerators.
+ *  zeta_batch_finish: wait for the stream, read the numerators back, run
+ *      the host finish; outputs as in zeta_batch.
+ *  zeta_batch_release: free the plan (NULL allowed). */
+typedef struct zeta_batch_plan zeta_batch_plan;
+zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                               zeta_batch_plan **out);
+zeta_status zeta_batch_run(zeta_ctx *ctx, zeta_batch_plan *plan);
+zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *plan, int64_t *P_out, size_t stride,
+                              zeta_stats *per_instance, zeta_stats *total);
+zeta_status zeta_batch_release(zeta_batch_plan *plan);
+
+/* Kernel-level entry point: Algorithm 2 on `count` independent problems
+ * held in DEVICE memory (parity tests of the recurrence kernels).
+ *  For problem t: W_t <- M(0) M(1) ... M(k_t - 1) W_t mod q_t with
+ *  M(y) = y A_t + B_t; A_t, B_t are s x s row-major at A + t*s*s, B + t*s*s;
+ *  W_t is s x c row-major at W + t*s*c (overwritten); k_t = k[t] >= 0;
+ *  q_t = q[t] in [2, 2^63).  Entries must be reduced mod q_t.
+ *  All pointers are device pointers; ZETA_ERR_ARG if s or c exceed the
+ *  kernel limits (s <= 512, c <= 32). */
+zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
+                               const uint32_t *k, const uint64_t *A, const uint64_t *B,
+                               uint64_t *W, const uint64_t *q);
+
+/* ---------------------------------------------------------------------------
+ * Host-only entry points (no device needed): the setup and finishing steps
+ * of the path, exposed so that they can be checked in isolation.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint32_t b, s, nv;          /* basis size, C(dn, n), n + 1 */
+    uint32_t sec_rows;          /* (n+1) * C(n(d-2)+n, n): rows (i, nu), i major */
+    uint32_t sec_cols;          /* C(kappa+n, n), kappa = (n+1)(d-2)+1 */
+    uint32_t h_rows;            /* C(dn-1, n): monomials of degree dn-n-1 */
+    uint32_t r, M;
+    uint64_t q;                 /* p^M */
+    uint64_t nchains, nterms;
+} zeta_plan_info;
+
+/* Host setup of one instance (Sec. 2.3-2.5, Prop. 2.1, Alg. 1, Prop. 3.3):
+ *  sec:        sec_rows x sec_cols uint64 (row-major) -- the section of the
+ *              Jacobian map M_kappa over Z/q: column gamma holds g_0..g_n with
+ *              sum_i g_i d_i f = x^gamma (rows (i, nu), nu in Homog_{n(d-2)}).
+ *  chain_U:    nchains x nv int32 -- start exponents U (Tweak of p(beta+alpha+1)),
+ *              distinct, longest first.
+ *  chain_terms:nchains x 2 uint32 -- [begin, end) ranges into the term arrays.
+ *  term_rc:    nterms x 2 uint32 -- (row = index of J in Homog_{dn-n}, basis column).
+ *  term_coeff: nterms uint64 -- (D_{j,m} C_{j,alpha} mod p^{s_m}) (p s_m - 1)!/(p(m+j) - 1)! mod q.
+ *  fin:        b x h_rows uint64 -- the final reduction map (Sec. 3.3 step (2))
+ *              from pole-order-n numerators to basis coordinates, mod q.
+ * Every buffer may be NULL (then it is not written); call once with NULLs
+ * to read the sizes from info. */
+zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta_plan_info *info,
+                      uint64_t *sec, int32_t *chain_U, uint32_t *chain_terms, uint32_t *term_rc,
+                      uint64_t *term_coeff, uint64_t *fin);
+
+/* Host finishing steps from accumulated pole-order-n numerators:
+ *  H: h_rows x b uint64 mod q -- column j holds the sum over all reduced
+ *     terms of column j of the numerators x^U g / x^S (degree dn-n-1).
+ *  Outputs as in zeta_frobenius / zeta_charpoly; any may be NULL. */
+zeta_status zeta_finish(const zeta_hypersurface *hs, const zeta_options *opt, const uint64_t *H,
+                        uint64_t *F_out, uint64_t *Y_out, int64_t *P_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZETA_H */

@@ -1,0 +1,318 @@
+// C ABI of the library (declared in include/zeta.h).  Marshalling, host
+// thread pool for the per-instance setup, and the device engine calls.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "zeta_internal.h"
+
+using namespace zeta;
+
+struct zeta_ctx {
+    DeviceEngine *engine = nullptr;
+    std::string error;
+    unsigned threads = 1;
+};
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void parallel_for(size_t count, unsigned threads, const std::function<void(size_t)> &fn) {
+    if (count == 0) return;
+    threads = (unsigned)std::min<size_t>(std::max(1u, threads), count);
+    if (threads == 1) {
+        for (size_t i = 0; i < count; i++) fn(i);
+        return;
+    }
+    std::atomic<size_t> next(0);
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < threads; t++)
+        pool.emplace_back([&]() {
+            for (size_t i = next++; i < count; i = next++) fn(i);
+        });
+    for (auto &th : pool) th.join();
+}
+
+static void fill_stats(const Instance &X, zeta_stats *st, double ms_device) {
+    if (!st) return;
+    std::memset(st, 0, sizeof(*st));
+    st->status = (int32_t)X.status;
+    st->b = X.b;
+    st->r = X.r;
+    st->M = X.M;
+    for (int i = 0; i < 8; i++) st->N[i] = X.N[i];
+    st->s = X.s;
+    st->eps = X.eps;
+    st->chains = X.chains.size();
+    st->terms = X.nterms;
+    st->chunks = X.chunks;
+    st->steps = X.steps;
+    st->column_steps = X.column_steps;
+    st->ms_host_setup = X.ms_setup;
+    st->ms_device = ms_device;
+    st->ms_host_finish = X.ms_finish;
+}
+
+static zeta_options default_options() {
+    zeta_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.policy = ZETA_POLICY_DEPTH_FIRST;
+    o.path = ZETA_PATH_VECTOR;
+    return o;
+}
+
+extern "C" {
+
+zeta_status zeta_create(zeta_ctx **out, int device, void *cuda_stream) {
+    if (!out) return ZETA_ERR_ARG;
+    *out = nullptr;
+    zeta_ctx *c = new (std::nothrow) zeta_ctx();
+    if (!c) return ZETA_ERR_OOM;
+    std::string err;
+    c->engine = engine_create(device, cuda_stream, err);
+    if (!c->engine) {
+        delete c;
+        return ZETA_ERR_DEVICE;
+    }
+    c->threads = std::max(1u, std::thread::hardware_concurrency());
+    *out = c;
+    return ZETA_OK;
+}
+
+zeta_status zeta_destroy(zeta_ctx *ctx) {
+    if (!ctx) return ZETA_OK;
+    engine_destroy(ctx->engine);
+    delete ctx;
+    return ZETA_OK;
+}
+
+const char *zeta_last_error(const zeta_ctx *ctx) {
+    if (!ctx) return "null context";
+    return ctx->error.c_str();
+}
+
+zeta_status zeta_query(const zeta_hypersurface *hs, const zeta_options *opt, uint32_t *b, uint32_t *r,
+                       uint32_t *M, uint32_t *s) {
+    if (!hs) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    zeta_status st = prepare_instance(hs, &o, false, X);
+    if (st) return st;
+    if (b) *b = X.b;
+    if (r) *r = X.r;
+    if (M) *M = X.M;
+    if (s) *s = X.s;
+    return ZETA_OK;
+}
+
+static zeta_status run_one(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, Instance &X,
+                           double *ms_dev) {
+    zeta_options o = opt ? *opt : default_options();
+    zeta_status st = prepare_instance(hs, &o, true, X);
+    if (st) { ctx->error = X.error; return st; }
+    std::vector<Instance *> batch{&X};
+    st = engine_run(ctx->engine, batch, o.policy, o.path, ctx->error, ms_dev);
+    if (st) return st;
+    st = (o.flags & ZETA_FLAG_Y_ONLY) ? finish_y_only(X) : finish_instance(X);
+    if (st) { ctx->error = X.error; return st; }
+    return ZETA_OK;
+}
+
+zeta_status zeta_frobenius(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, uint64_t *F_out,
+                           uint64_t *Y_out, zeta_stats *stats) {
+    if (!ctx || !hs || !F_out) return ZETA_ERR_ARG;
+    Instance X;
+    double ms = 0;
+    zeta_status st = run_one(ctx, hs, opt, X, &ms);
+    if (st) return st;
+    if (!X.F.empty()) std::memcpy(F_out, X.F.data(), sizeof(uint64_t) * X.F.size());
+    else std::memset(F_out, 0, sizeof(uint64_t) * X.b * X.b);
+    if (Y_out) std::memcpy(Y_out, X.Y.data(), sizeof(uint64_t) * X.Y.size());
+    fill_stats(X, stats, ms);
+    return ZETA_OK;
+}
+
+static void write_coeff(int64_t *dst, i128 v) {
+    dst[0] = (int64_t)(uint64_t)((u128)v & 0xFFFFFFFFFFFFFFFFull);
+    dst[1] = (int64_t)(v >> 64);
+}
+
+zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, int64_t *P_out,
+                          zeta_stats *stats) {
+    if (!ctx || !hs || !P_out) return ZETA_ERR_ARG;
+    Instance X;
+    double ms = 0;
+    zeta_status st = run_one(ctx, hs, opt, X, &ms);
+    if (st) return st;
+    for (uint32_t i = 0; i <= X.b; i++) write_coeff(P_out + 2 * i, i < X.P.size() ? X.P[i] : 0);
+    fill_stats(X, stats, ms);
+    return ZETA_OK;
+}
+
+}  // extern "C"
+
+struct zeta_batch_plan {
+    std::vector<Instance> inst;
+    std::vector<Instance *> ok;
+    zeta_options opt;
+    DeviceBatch *dev = nullptr;
+    double ms_setup = 0, ms_device = 0;
+    bool launched = false;
+};
+
+extern "C" {
+
+zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                               zeta_batch_plan **out) {
+    if (!ctx || !out || (!hs && count)) return ZETA_ERR_ARG;
+    *out = nullptr;
+    zeta_batch_plan *P = new (std::nothrow) zeta_batch_plan();
+    if (!P) return ZETA_ERR_OOM;
+    P->opt = opt ? *opt : default_options();
+    P->inst.resize(count);
+    double t0 = now_ms();
+    parallel_for(count, ctx->threads, [&](size_t i) { prepare_instance(&hs[i], &P->opt, true, P->inst[i]); });
+    for (auto &X : P->inst)
+        if (X.status == ZETA_OK) P->ok.push_back(&X);
+        else if (ctx->error.empty()) ctx->error = X.error;
+    P->ms_setup = now_ms() - t0;
+    if (!P->ok.empty()) {
+        zeta_status st = engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, &P->dev, ctx->error);
+        if (st) { delete P; return st; }
+    }
+    *out = P;
+    return ZETA_OK;
+}
+
+zeta_status zeta_batch_run(zeta_ctx *ctx, zeta_batch_plan *P) {
+    if (!ctx || !P) return ZETA_ERR_ARG;
+    if (!P->dev) return ZETA_OK;
+    P->launched = true;
+    return engine_launch(ctx->engine, P->dev, ctx->error);
+}
+
+zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *P, int64_t *P_out, size_t stride,
+                              zeta_stats *per_instance, zeta_stats *total) {
+    if (!ctx || !P || (!P_out && !P->inst.empty())) return ZETA_ERR_ARG;
+    for (Instance *X : P->ok)
+        if ((size_t)X->b + 1 > stride) return ZETA_ERR_ARG;
+    if (P->dev) {
+        if (!P->launched) {
+            zeta_status st = engine_launch(ctx->engine, P->dev, ctx->error);
+            if (st) return st;
+        }
+        zeta_status st = engine_collect(ctx->engine, P->dev, ctx->error);
+        if (st) return st;
+    }
+    double t2 = now_ms();
+    bool y_only = (P->opt.flags & ZETA_FLAG_Y_ONLY) != 0;
+    parallel_for(P->ok.size(), ctx->threads, [&](size_t i) {
+        if (y_only) finish_y_only(*P->ok[i]);
+        else finish_instance(*P->ok[i]);
+    });
+    double t3 = now_ms();
+    zeta_stats agg;
+    std::memset(&agg, 0, sizeof(agg));
+    for (size_t i = 0; i < P->inst.size(); i++) {
+        Instance &X = P->inst[i];
+        if (X.status == ZETA_OK) {
+            for (uint32_t t = 0; t <= X.b; t++)
+                write_coeff(P_out + 2 * (i * stride + t), t < X.P.size() ? X.P[t] : 0);
+        } else if (ctx->error.empty()) {
+            ctx->error = X.error;
+        }
+        if (per_instance) fill_stats(X, &per_instance[i], 0);
+        if (X.status == ZETA_OK) {
+            agg.chains += X.chains.size();
+            agg.terms += X.nterms;
+            agg.chunks += X.chunks;
+            agg.steps += X.steps;
+            agg.column_steps += X.column_steps;
+        }
+    }
+    agg.ms_host_setup = P->ms_setup;
+    agg.ms_host_finish = t3 - t2;
+    engine_batch_timing(P->dev, &agg.ms_kernel, &agg.kernel_launches, &agg.bytes_h2d, &agg.bytes_d2h);
+    if (total) *total = agg;
+    return ZETA_OK;
+}
+
+zeta_status zeta_batch_release(zeta_batch_plan *P) {
+    if (!P) return ZETA_OK;
+    engine_release(P->dev);
+    delete P;
+    return ZETA_OK;
+}
+
+zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                       int64_t *P_out, size_t stride, zeta_stats *per_instance, zeta_stats *total) {
+    if (!ctx || (!hs && count) || (!P_out && count)) return ZETA_ERR_ARG;
+    zeta_batch_plan *P = nullptr;
+    zeta_status st = zeta_batch_prepare(ctx, hs, count, opt, &P);
+    if (st) return st;
+    st = zeta_batch_run(ctx, P);
+    if (!st) st = zeta_batch_finish(ctx, P, P_out, stride, per_instance, total);
+    zeta_batch_release(P);
+    return st;
+}
+
+zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
+                               const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
+                               const uint64_t *q) {
+    if (!ctx || (count && (!k || !A || !B || !W || !q))) return ZETA_ERR_ARG;
+    return engine_horner(ctx->engine, path, count, s, c, k, A, B, W, q, ctx->error);
+}
+
+zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta_plan_info *info, uint64_t *sec,
+                      int32_t *chain_U, uint32_t *chain_terms, uint32_t *term_rc, uint64_t *term_coeff,
+                      uint64_t *fin) {
+    if (!hs) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    zeta_status st = prepare_instance(hs, &o, true, X);
+    if (st) return st;
+    if (info) {
+        info->b = X.b; info->s = X.s; info->nv = X.nv;
+        info->sec_rows = X.sec_rows; info->sec_cols = X.sec_cols; info->h_rows = X.h_rows;
+        info->r = X.r; info->M = X.M; info->q = X.q;
+        info->nchains = X.chains.size(); info->nterms = X.terms.size();
+    }
+    if (sec) std::memcpy(sec, X.sec.data(), sizeof(uint64_t) * X.sec.size());
+    for (size_t c = 0; c < X.chains.size(); c++) {
+        if (chain_U)
+            for (uint32_t t = 0; t < X.nv; t++) chain_U[c * X.nv + t] = X.chains[c].U[t];
+        if (chain_terms) { chain_terms[2 * c] = X.chains[c].term_begin; chain_terms[2 * c + 1] = X.chains[c].term_end; }
+    }
+    for (size_t t = 0; t < X.terms.size(); t++) {
+        if (term_rc) { term_rc[2 * t] = X.terms[t].row; term_rc[2 * t + 1] = X.terms[t].col; }
+        if (term_coeff) term_coeff[t] = X.terms[t].coeff;
+    }
+    if (fin) std::memcpy(fin, X.fin.data(), sizeof(uint64_t) * X.fin.size());
+    return ZETA_OK;
+}
+
+zeta_status zeta_finish(const zeta_hypersurface *hs, const zeta_options *opt, const uint64_t *H, uint64_t *F_out,
+                        uint64_t *Y_out, int64_t *P_out) {
+    if (!hs || !H) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    zeta_status st = prepare_instance(hs, &o, true, X);
+    if (st) return st;
+    X.H.assign(H, H + (size_t)X.h_rows * X.b);
+    st = finish_instance(X);
+    if (st) return st;
+    if (F_out) std::memcpy(F_out, X.F.data(), sizeof(uint64_t) * X.F.size());
+    if (Y_out) std::memcpy(Y_out, X.Y.data(), sizeof(uint64_t) * X.Y.size());
+    if (P_out)
+        for (uint32_t i = 0; i <= X.b; i++) write_coeff(P_out + 2 * i, X.P[i]);
+    return ZETA_OK;
+}
+
+}  // extern "C"

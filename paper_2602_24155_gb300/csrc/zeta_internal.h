@@ -1,0 +1,92 @@
+// Internal interfaces between the host setup (zeta_host.cpp) and the CUDA
+// kernels (zeta_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/zeta.h"
+
+namespace zeta {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+constexpr int kMaxVars = 8;
+
+// ---------------------------------------------------------------------------
+// Per-instance data prepared on the host (Prop. 2.1, Alg. 1, Prop. 3.3).
+// ---------------------------------------------------------------------------
+struct Term {
+    uint32_t row;    // index of J in Homog_{dn-n} (descending lex)
+    uint32_t col;    // basis column
+    uint64_t coeff;  // mod q
+};
+
+struct Chain {
+    int32_t U[kMaxVars];     // start exponent (pole order (|U|-n)/d + n)
+    uint32_t term_begin, term_end;
+    uint64_t work;           // estimated steps * s^2 * b
+};
+
+struct Instance {
+    // input
+    uint32_t n = 0, d = 0, p = 0, nv = 0;
+    std::vector<uint32_t> coeffs;
+    // sizes
+    uint32_t b = 0, s = 0;       // basis size, |Homog_{dn-n}|
+    uint32_t kappa = 0;          // (n+1)(d-2)+1
+    uint32_t sec_rows = 0, sec_cols = 0;
+    uint32_t h_rows = 0;         // |Homog_{dn-n-1}|
+    // precision
+    uint32_t r = 0, M = 0;             // r = max_m r_m
+    uint32_t rm[kMaxVars] = {0};       // r_m, m = 1..n (index m-1)
+    uint32_t N[kMaxVars] = {0};
+    uint64_t q = 0;
+    std::vector<uint32_t> pole;  // pole order of each basis element
+    std::vector<std::vector<int>> basis_exp;
+    // controlled reduction data
+    std::vector<uint64_t> sec;   // sec_rows x sec_cols, Sec[(i,nu), gamma]
+    std::vector<Chain> chains;
+    std::vector<Term> terms;
+    std::vector<uint64_t> fin;   // b x h_rows final reduction map mod q
+    // results
+    std::vector<uint64_t> H;     // h_rows x b accumulated numerators mod q
+    std::vector<uint64_t> Y;     // b x b
+    std::vector<uint64_t> F;     // b x b
+    std::vector<i128> P;         // b+1
+    int eps = 0;
+    zeta_status status = ZETA_OK;
+    std::string error;
+    uint64_t nterms = 0, steps = 0, column_steps = 0, chunks = 0;
+    double ms_setup = 0, ms_finish = 0;
+};
+
+// Host-side steps (zeta_host.cpp)
+zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *opt,
+                             bool build_reduction, Instance &X);
+zeta_status finish_instance(Instance &X);
+zeta_status finish_y_only(Instance &X);  // Y = Fin * H only
+
+// Device engine (zeta_kernels.cu): runs the recurrence for every chain of
+// every instance and fills X.H.  `policy` selects the reduction policy.
+struct DeviceEngine;
+DeviceEngine *engine_create(int device, void *stream, std::string &err);
+void engine_destroy(DeviceEngine *e);
+zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy,
+                       zeta_path path, std::string &err, double *ms_device);
+// The same in three phases: upload (inputs become resident in device
+// memory), launch (kernels only, asynchronous on the engine's stream),
+// collect (synchronise and read H back).
+struct DeviceBatch;
+zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
+                           DeviceBatch **out, std::string &err);
+zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err);
+zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err);
+void engine_release(DeviceBatch *B);
+void engine_batch_timing(const DeviceBatch *B, double *ms_kernel, uint64_t *launches, uint64_t *h2d, uint64_t *d2h);
+zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
+                          const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
+                          const uint64_t *q, std::string &err);
+
+}  // namespace zeta

@@ -1,0 +1,114 @@
+"""CPU checks of the library's host steps (setup and finish) against the oracle.
+
+The device recurrence is replayed here in plain Python on the plan the
+library exports (start terms, section, final map): depth-first chunks with
+step matrices generated from the section by the monomial formula
+  R_{u,v}[omega, mu] = sum_i (u_i + omega_i) Sec[(i, omega - 1 + e_i), v + mu - 1],
+then the library's own finishing step.  Agreement of Y and P(T) with the
+oracle checks the host setup, the formula and the finish without a GPU.
+"""
+import numpy as np
+import pytest
+
+import zeta_inputs as zi
+from oracle import cohomology, zeta as ozeta
+from oracle.algebra import monomials
+from oracle.policies import greedy_v, k_max
+
+z = pytest.importorskip("paper_2602_24155_gb300")
+
+
+def _rank_table(nv, deg):
+    return {m: i for i, m in enumerate(monomials(nv, deg))}
+
+
+def replay(spec, plan):
+    n, d, p, coeffs = spec
+    nv = n + 1
+    q = int(plan["q"])
+    b = plan["b"]
+    mS = monomials(nv, d * n - n)
+    s = len(mS)
+    src = _rank_table(nv, n * (d - 2))
+    kap = _rank_table(nv, (n + 1) * (d - 2) + 1)
+    hpos = _rank_table(nv, d * n - n - 1)
+    nsrc = len(src)
+    sec = plan["sec"].astype(object)
+    H = np.zeros((len(hpos), b), dtype=object)
+    for ci in range(plan["U"].shape[0]):
+        U = tuple(int(x) for x in plan["U"][ci])
+        W = np.zeros((s, b), dtype=object)
+        t0, t1 = plan["chain_terms"][ci]
+        for t in range(t0, t1):
+            r, c = plan["term_rc"][t]
+            W[r, c] = (W[r, c] + int(plan["term_coeff"][t])) % q
+        while sum(U) > n:
+            v = greedy_v(d, U, set(range(nv)))
+            k = k_max(U, v, n, d)
+            x = tuple(a - k * bb for a, bb in zip(U, v))
+            A = np.zeros((s, s), dtype=object)
+            B = np.zeros((s, s), dtype=object)
+            for j, mu in enumerate(mS):
+                g = tuple(v[t] + mu[t] - 1 for t in range(nv))
+                if min(g) < 0:
+                    continue
+                col = kap[g]
+                for r, om in enumerate(mS):
+                    a = bb = 0
+                    for i in range(nv):
+                        nu = tuple(om[t] - 1 + (1 if t == i else 0) for t in range(nv))
+                        if min(nu) < 0:
+                            continue
+                        val = sec[i * nsrc + src[nu], col]
+                        a += v[i] * val
+                        bb += (x[i] + om[i]) * val
+                    A[r, j] = a % q
+                    B[r, j] = bb % q
+            W = ozeta.horner_python(A, B, W, k, q)
+            U = x
+        for j, mu in enumerate(mS):
+            g = tuple(U[t] + mu[t] - 1 for t in range(nv))
+            if min(g) < 0:
+                continue
+            H[hpos[g]] = (H[hpos[g]] + W[j]) % q
+    return H.astype(np.uint64)
+
+
+def test_plan_sizes_match_oracle_precision():
+    n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
+    b, r, M, s = z.zeta_query((n, d, p, c))
+    res = ozeta.compute_zeta(n, d, p, c, want_P=False)
+    assert (b, r, M) == (len(res.basis), max(res.prec.r.values()), res.prec.M)
+    assert s == 28
+    for i in range(1, 4):
+        n, d, p, c, _ = zi.draw_instance("quintic_curves", i, cohomology.is_smooth)
+        from oracle.precision import Precision
+        X = cohomology.Hypersurface(n, d, p, c)
+        basis = cohomology.cohomology_basis(X)
+        pr = Precision(n, d, p, [m for m, _ in basis])
+        assert z.zeta_query((n, d, p, c))[:3] == (len(basis), max(pr.r.values()), pr.M)
+
+
+def test_replayed_plan_matches_oracle_quartic():
+    n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
+    spec = (n, d, p, c)
+    plan = z.zeta_plan(spec)
+    H = replay(spec, plan)
+    F, Y, P = z.zeta_finish(spec, H)
+    res = ozeta.compute_zeta(n, d, p, c)
+    assert (Y.astype(object) == res.Y).all()
+    assert P == res.P
+    assert (F.astype(object) == res.F).all()
+
+
+def test_non_smooth_and_unsupported_inputs_are_rejected():
+    c = [1 if m in [(4, 0, 0), (0, 4, 0)] else 0 for m in monomials(3, 4)]
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((2, 4, 7, c))
+    assert e.value.status == 2
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((2, 4, 5, zi.fermat(2, 4)))       # p < 7
+    assert e.value.status == 3
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((2, 4, 11, [11] + [0] * 14))      # coefficient not reduced
+    assert e.value.status == 1
