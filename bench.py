@@ -169,7 +169,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--policy", default="depth_first")
+    ap.add_argument("--policy", default="p_chunk")
     ap.add_argument("--path", default="vector")
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

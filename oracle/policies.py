@@ -129,6 +129,10 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
             out.append((u, w))
         return out
     if policy == "p_chunk":
+        # Reading of Sec. 4.1: every term of the largest pole order K is reduced
+        # by a chunk of size p (p - n when K = p, i.e. down to pole order n);
+        # when the greedy direction admits fewer steps, the chunk is completed
+        # with further greedy directions, so all terms stay on pole orders p t.
         live = merge_terms(terms, add, log)
         done = []
         while live:
@@ -136,12 +140,15 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
             nxt = []
             for u, w in live:
                 if sum(u) == L:
-                    v = greedy_v(d, u, S)
                     K = pole_order(u, n, d)
-                    k = min(p, K - n, k_max(u, v, n, d))
-                    assert k >= 1 and in_V_full(u, v, k, S)
-                    w = reduce_chunk(u, v, k, w)
-                    u = sub_kv(u, v, k)
+                    left = K - max(K - p, n)
+                    while left > 0:
+                        v = greedy_v(d, u, S)
+                        k = min(left, k_max(u, v, n, d))
+                        assert k >= 1 and in_V_full(u, v, k, S)
+                        w = reduce_chunk(u, v, k, w)
+                        u = sub_kv(u, v, k)
+                        left -= k
                 nxt.append((u, w))
             nxt = merge_terms(nxt, add, log)
             done += [(u, w) for u, w in nxt if sum(u) == n]

@@ -116,6 +116,7 @@ static zeta_status run_one(zeta_ctx *ctx, const zeta_hypersurface *hs, const zet
                            double *ms_dev) {
     zeta_options o = opt ? *opt : default_options();
     zeta_status st = prepare_instance(hs, &o, true, X);
+    if (!st) st = schedule_policy(X, o.policy);
     if (st) { ctx->error = X.error; return st; }
     std::vector<Instance *> batch{&X};
     st = engine_run(ctx->engine, batch, o.policy, o.path, ctx->error, ms_dev);
@@ -178,7 +179,9 @@ zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_
     P->opt = opt ? *opt : default_options();
     P->inst.resize(count);
     double t0 = now_ms();
-    parallel_for(count, ctx->threads, [&](size_t i) { prepare_instance(&hs[i], &P->opt, true, P->inst[i]); });
+    parallel_for(count, ctx->threads, [&](size_t i) {
+        if (prepare_instance(&hs[i], &P->opt, true, P->inst[i]) == ZETA_OK) schedule_policy(P->inst[i], P->opt.policy);
+    });
     for (auto &X : P->inst)
         if (X.status == ZETA_OK) P->ok.push_back(&X);
         else if (ctx->error.empty()) ctx->error = X.error;

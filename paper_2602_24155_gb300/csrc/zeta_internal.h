@@ -29,6 +29,36 @@ struct Chain {
     uint64_t work;           // estimated steps * s^2 * b
 };
 
+// A reduction plan: the game of Sec. 3.4 played on the host (integer-only),
+// executed on the device.  Phases run in order; within a phase every entry is
+// one term: its W block is formed from an arrival block (the merged results
+// of the previous phase that landed on this exponent) and/or the start terms
+// of one chain, then reduced by its chunk list (move 1: k steps in direction
+// v, Sec. 3.4), then merged into a block of the next phase (move 2) or, at
+// pole order n, accumulated into the numerators H.
+struct PlanChunk {
+    int8_t v[kMaxVars];
+    int32_t k;
+};
+
+struct PlanEntry {
+    int32_t U[kMaxVars];         // exponent at the start of the phase
+    uint32_t chunk_begin, chunk_end;
+    int32_t arrival;             // block of the current phase buffer, or -1
+    int32_t start_chain;         // chain whose start terms join here, or -1
+    int32_t dest;                // block of the next phase buffer, -1: pole order n reached
+    uint32_t flags;              // bit 0: first contribution to dest (store, not add)
+    uint32_t live;               // basis columns carried (bit mask, b <= 32)
+};
+
+struct Plan {
+    std::vector<PlanEntry> entries;
+    std::vector<PlanChunk> chunks;
+    std::vector<uint32_t> phase_begin;  // nphases + 1 offsets into entries
+    uint32_t cap = 0;                   // blocks per phase buffer
+    uint64_t chunks_played = 0, steps = 0, column_steps = 0, merges = 0, work = 0;
+};
+
 struct Instance {
     // input
     uint32_t n = 0, d = 0, p = 0, nv = 0;
@@ -50,6 +80,7 @@ struct Instance {
     std::vector<Chain> chains;
     std::vector<Term> terms;
     std::vector<uint64_t> fin;   // b x h_rows final reduction map mod q
+    Plan plan;
     // results
     std::vector<uint64_t> H;     // h_rows x b accumulated numerators mod q
     std::vector<uint64_t> Y;     // b x b
@@ -66,6 +97,8 @@ struct Instance {
 zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *opt,
                              bool build_reduction, Instance &X);
 zeta_status finish_instance(Instance &X);
+// Plays the policy on the start chains of X and fills X.plan (zeta_policy.cpp).
+zeta_status schedule_policy(Instance &X, zeta_policy policy);
 zeta_status finish_y_only(Instance &X);  // Y = Fin * H only
 
 // Device engine (zeta_kernels.cu): runs the recurrence for every chain of

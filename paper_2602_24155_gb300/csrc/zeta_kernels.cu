@@ -42,7 +42,6 @@ namespace zeta {
         }                                                                                \
     } while (0)
 
-constexpr int kThreads = 256;
 constexpr int kMaxS = 512;
 constexpr int kMaxC = 32;
 
@@ -52,8 +51,8 @@ constexpr int kMaxC = 32;
 struct ModQ {
     uint64_t q;
     uint64_t qneg_inv;  // -q^{-1} mod 2^64
-    uint64_t r2;        // 2^128 mod q
-    uint64_t k[3];      // 2^128 * 2^{30 t} mod q, t = 0, 1, 2
+    uint64_t r2;        // 2^128 mod q  (R^2, R = 2^64)
+    uint64_t k30;       // 2^30 R mod q
 };
 
 __device__ __forceinline__ uint64_t mul_hi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
@@ -94,86 +93,118 @@ __device__ __forceinline__ void add128(uint64_t &lo, uint64_t &hi, uint64_t x) {
     hi += (lo < x) ? 1ull : 0ull;
 }
 
-// out = T0 + T1 2^30 + T2 2^60 mod q, each T_t a 128-bit value below q 2^64.
-__device__ __forceinline__ uint64_t fold_limbs(const uint64_t T[6], const ModQ &Q) {
-    uint64_t out = 0;
-#pragma unroll
-    for (int t = 0; t < 3; t++) {
-        uint64_t y = redc(T[2 * t], T[2 * t + 1], Q);  // T_t 2^{-64}
-        uint64_t z = redc(y * Q.k[t], mul_hi64(y, Q.k[t]), Q);  // T_t 2^{30t} mod q
-        out = addmod(out, z, Q.q);
-    }
-    return out;
+// Limb layout of the recurrence.
+//  W entries: 30-bit limbs (w0, w1) in a uint2 (q < 2^60), ordinary residues.
+//  M entries: Montgomery form M R mod q in uint64, split on load into 20-bit
+//             limbs m0, m1, m2.
+// A limb product is below 2^50, so the six partial sums
+//   S[t] = sum_j m_{t/2}(j) w_{t%2}(j)  (weights 2^{20 (t/2) + 30 (t%2)})
+// stay below 2^59 for s <= 512 in plain uint64 registers.
+// X = sum_j m_j w0_j and Y = sum_j m_j w1_j are each below s q 2^30 < q 2^64,
+// so one Montgomery reduction (REDC, R = 2^64) applies to each:
+//   (M W)_r = REDC(X) + REDC(REDC(Y) * (2^30 R mod q))  mod q.
+__device__ __forceinline__ void madw(uint64_t &acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+__device__ __forceinline__ uint64_t fold_partials(const uint64_t S[6], const ModQ &Q) {
+    uint64_t xl = S[0], xh = 0, yl = S[1], yh = 0;
+    add128(xl, xh, S[2] << 20); xh += S[2] >> 44;
+    add128(xl, xh, S[4] << 40); xh += S[4] >> 24;
+    add128(yl, yh, S[3] << 20); yh += S[3] >> 44;
+    add128(yl, yh, S[5] << 40); yh += S[5] >> 24;
+    const uint64_t xr = redc(xl, xh, Q);   // X R^{-1}
+    const uint64_t yr = redc(yl, yh, Q);   // Y R^{-1}
+    const uint64_t c = redc(yr * Q.k30, mul_hi64(yr, Q.k30), Q);  // Y 2^30 R^{-1}
+    return addmod(xr, c, Q.q);
+}
+
+// a R mod q (to Montgomery form)
+__device__ __forceinline__ uint64_t to_mont(uint64_t a, const ModQ &Q) {
+    return redc(a * Q.r2, mul_hi64(a, Q.r2), Q);
 }
 
 // ---------------------------------------------------------------------------
 // One block-wide evaluation of k steps of Algorithm 2.
-//  Mt, At: s x s stored transposed (entry (row r, col j) at [j*s + r]); Mt
-//          holds M(k-1) = (k-1)A + B on entry and is consumed.
-//  W0/W1 : shared memory limbs (low 30 bits / high bits) of W, s x c, [j*c + col];
-//  V0/V1 : second buffer of the same shape.  On return the result is in the
-//          buffer returned (0 = W, 1 = V).
+//  Ms, As: s x s uint64 in Montgomery form, entry (row r, col j) at
+//          [j*s + r] (shared memory for small s, global scratch otherwise);
+//          Ms holds M(k-1) R = ((k-1)A + B) R on entry and is consumed
+//          (M <- M - A).
+//  W, V  : s x c limb pairs in shared memory, [j*c + col]; the input is in
+//          W; the output is in the buffer returned (0 = W, 1 = V).
+// Thread item = (row r, group of CPT consecutive columns).
 // ---------------------------------------------------------------------------
 template <int CPT>
-__device__ int horner_block(int s, int c, int k, uint64_t *Mt, const uint64_t *At,
-                            uint32_t *W0, uint32_t *W1, uint32_t *V0, uint32_t *V1, const ModQ &Q) {
+__device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *As, uint2 *W, uint2 *V,
+                            const ModQ &Q) {
     const int ngroups = (c + CPT - 1) / CPT;
     const int items = s * ngroups;
-    const uint32_t MASK = (1u << 30) - 1;
+    const uint32_t MASK20 = (1u << 20) - 1, MASK30 = (1u << 30) - 1;
     int cur = 0;
     for (int step = 0; step < k; step++) {
-        uint32_t *in0 = cur ? V0 : W0, *in1 = cur ? V1 : W1;
-        uint32_t *out0 = cur ? W0 : V0, *out1 = cur ? W1 : V1;
+        const uint2 *in = cur ? V : W;
+        uint2 *out = cur ? W : V;
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int r = it % s;
-            const int g = it / s;
-            const int c0 = g * CPT;
-            uint64_t T[CPT][6];
+            const int c0 = (it / s) * CPT;
+            const int nc = min(CPT, c - c0);
+            uint64_t S[CPT][6];
 #pragma unroll
             for (int cc = 0; cc < CPT; cc++)
 #pragma unroll
-                for (int t = 0; t < 6; t++) T[cc][t] = 0;
-            for (int jb = 0; jb < s; jb += 4) {
-                uint64_t S[CPT][3];
-#pragma unroll
-                for (int cc = 0; cc < CPT; cc++) S[cc][0] = S[cc][1] = S[cc][2] = 0;
-                const int jend = min(jb + 4, s);
-                for (int j = jb; j < jend; j++) {
-                    const uint64_t m = Mt[(size_t)j * s + r];
-                    const uint32_t m0 = (uint32_t)m & MASK;
-                    const uint32_t m1 = (uint32_t)(m >> 30);
+                for (int t = 0; t < 6; t++) S[cc][t] = 0;
+            const uint64_t *mcol = Ms + r;
+            const uint2 *wrow = in + c0;
+            if (nc == CPT) {
+                for (int j = 0; j < s; j++) {
+                    const uint64_t m = mcol[(size_t)j * s];
+                    const uint32_t m0 = (uint32_t)m & MASK20;
+                    const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
+                    const uint32_t m2 = (uint32_t)(m >> 40);
+                    const uint2 *wj = wrow + j * c;
 #pragma unroll
                     for (int cc = 0; cc < CPT; cc++) {
-                        const int col = c0 + cc;
-                        if (col < c) {
-                            const uint32_t w0 = in0[j * c + col];
-                            const uint32_t w1 = in1[j * c + col];
-                            S[cc][0] += (uint64_t)m0 * w0;
-                            S[cc][1] += (uint64_t)m0 * w1 + (uint64_t)m1 * w0;
-                            S[cc][2] += (uint64_t)m1 * w1;
-                        }
+                        const uint2 w = wj[cc];
+                        madw(S[cc][0], m0, w.x);
+                        madw(S[cc][1], m0, w.y);
+                        madw(S[cc][2], m1, w.x);
+                        madw(S[cc][3], m1, w.y);
+                        madw(S[cc][4], m2, w.x);
+                        madw(S[cc][5], m2, w.y);
                     }
                 }
+            } else {
+                for (int j = 0; j < s; j++) {
+                    const uint64_t m = mcol[(size_t)j * s];
+                    const uint32_t m0 = (uint32_t)m & MASK20;
+                    const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
+                    const uint32_t m2 = (uint32_t)(m >> 40);
+                    const uint2 *wj = wrow + j * c;
 #pragma unroll
-                for (int cc = 0; cc < CPT; cc++) {
-                    add128(T[cc][0], T[cc][1], S[cc][0]);
-                    add128(T[cc][2], T[cc][3], S[cc][1]);
-                    add128(T[cc][4], T[cc][5], S[cc][2]);
+                    for (int cc = 0; cc < CPT; cc++) {
+                        if (cc < nc) {
+                            const uint2 w = wj[cc];
+                            madw(S[cc][0], m0, w.x);
+                            madw(S[cc][1], m0, w.y);
+                            madw(S[cc][2], m1, w.x);
+                            madw(S[cc][3], m1, w.y);
+                            madw(S[cc][4], m2, w.x);
+                            madw(S[cc][5], m2, w.y);
+                        }
+                    }
                 }
             }
 #pragma unroll
             for (int cc = 0; cc < CPT; cc++) {
-                const int col = c0 + cc;
-                if (col < c) {
-                    uint64_t v = fold_limbs(T[cc], Q);
-                    out0[r * c + col] = (uint32_t)v & MASK;
-                    out1[r * c + col] = (uint32_t)(v >> 30);
+                if (cc < nc) {
+                    const uint64_t v = fold_partials(S[cc], Q);
+                    out[r * c + c0 + cc] = make_uint2((uint32_t)v & MASK30, (uint32_t)(v >> 30));
                 }
             }
         }
         __syncthreads();
         if (step + 1 < k) {
-            for (int e = threadIdx.x; e < s * s; e += blockDim.x) Mt[e] = submod(Mt[e], At[e], Q.q);
+            for (int e = threadIdx.x; e < s * s; e += blockDim.x) Ms[e] = submod(Ms[e], As[e], Q.q);
             __syncthreads();
         }
         cur ^= 1;
@@ -190,6 +221,10 @@ struct DInst {
     uint32_t sec_cols, h_rows, kappa;
     uint32_t tab;          // table set index
     uint64_t sec_off;      // into sec pool
+    uint32_t phase_off;    // into the phase offset pool: nphases + 1 entry offsets
+    uint32_t nphases;
+    uint32_t chain_base;   // global index of the instance's first chain
+    uint32_t chunk_base;   // global index of the instance's first plan chunk
 };
 
 struct DTab {
@@ -207,6 +242,18 @@ struct DItem {
     uint32_t inst;
     uint32_t chain_begin, chain_end;
     uint32_t slot;         // partial H slot
+};
+
+struct DEntry {
+    int32_t U[kMaxVars];
+    uint32_t chunk_begin, chunk_end;  // instance-relative
+    int32_t arrival, start_chain, dest;
+    uint32_t flags, live;
+};
+
+struct DChunk {
+    int8_t v[kMaxVars];
+    int32_t k;
 };
 
 __constant__ int32_t c_binom[64][9];  // C(a, b) for a < 64, b <= 8
@@ -240,148 +287,203 @@ __device__ void greedy_chunk(const int *U, int nv, int n, int d, int *v, int *k_
     *k_out = k;
 }
 
-// Shared-memory layout of the chain kernel (bytes)
-__host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
-    return (size_t)4 * s * c * sizeof(uint32_t) + (size_t)h_rows * c * sizeof(uint64_t) + (size_t)s * sizeof(int) + 64;
+// Matrices M and A go to shared memory when both fit in this budget.
+constexpr size_t kMatSmemBudget = 96 * 1024;
+__host__ __device__ inline bool mats_in_smem(int s) { return (size_t)2 * s * s * sizeof(uint64_t) <= kMatSmemBudget; }
+
+// Threads per block: one per (row, group of 4 columns) item, rounded to warps, 64..512.
+inline int launch_threads(int s, int c) {
+    int items = s * ((c + 3) / 4);
+    int t = ((items + 31) / 32) * 32;
+    return std::max(64, std::min(512, t));
 }
 
-// Persistent kernel: each block takes work items (ranges of chains of one
-// instance) from a queue and plays the depth-first policy (Sec. 4.2) on
-// each chain to pole order n, accumulating x^U g / x^S into H.
-template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_depth_first(
+// Shared-memory layout of the chain kernel (bytes): [M A] (if small), W, V,
+// H partial, column map, colidx.
+__host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
+    size_t bytes = 0;
+    if (mats_in_smem(s)) bytes += (size_t)2 * s * s * sizeof(uint64_t);
+    bytes += (size_t)2 * s * c * sizeof(uint2);
+    bytes += (size_t)h_rows * c * sizeof(uint64_t);
+    bytes += (size_t)(c + s) * sizeof(int) + 64;
+    return bytes;
+}
+
+// Persistent plan executor.  Each block takes instances from a queue
+// (largest work first) and runs the instance's plan: phase after phase,
+// entry after entry: form W from the arrival block and/or the start terms,
+// play the entry's chunks (Algorithm 2 per chunk with matrices generated from
+// the section), then store or add the result into the destination block of
+// the next phase, or accumulate x^U g / x^S into H at pole order n.  One
+// block owns an instance, so merges need no atomics.
+template <int CPT, bool MSMEM>
+__global__ void __launch_bounds__(512) k_execute(
     const DInst *__restrict__ insts, const DTab *__restrict__ tabs, const int32_t *__restrict__ tabpool,
     const uint64_t *__restrict__ secpool, const DChain *__restrict__ chains, const Term *__restrict__ terms,
-    const DItem *__restrict__ items, uint32_t nitems, uint32_t *__restrict__ queue,
-    uint64_t *__restrict__ scratch, size_t scratch_stride, uint64_t *__restrict__ partial,
-    size_t partial_stride, unsigned long long *__restrict__ counters) {
+    const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
+    const uint32_t *__restrict__ order, uint32_t ninst, uint32_t *__restrict__ queue,
+    uint64_t *__restrict__ scratch, size_t scratch_stride, uint64_t *__restrict__ blocks, size_t blocks_stride,
+    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int sU[kMaxVars], sv[kMaxVars], sx[kMaxVars], sk;
+    __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
-    uint64_t *Mt = scratch + (size_t)blockIdx.x * scratch_stride;
     unsigned long long my_chunks = 0, my_steps = 0;
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         __syncthreads();
         const uint32_t itx = s_item;
         __syncthreads();
-        if (itx >= nitems) break;
-        const DItem item = items[itx];
-        const DInst I = insts[item.inst];
+        if (itx >= ninst) break;
+        const uint32_t inst = order[itx];
+        const DInst I = insts[inst];
         const DTab T = tabs[I.tab];
-        const int s = (int)I.s, c = (int)I.b, nv = (int)I.nv, n = (int)I.n, d = (int)I.d;
+        const int s = (int)I.s, b = (int)I.b, nv = (int)I.nv, n = (int)I.n, d = (int)I.d;
         const int32_t *monoS = tabpool + T.monoS_off;
         const int32_t *secrow = tabpool + T.secrow_off;
         const uint64_t *Sec = secpool + I.sec_off;
-        uint64_t *At = Mt + (size_t)s * s;
-        uint32_t *W0 = (uint32_t *)smem_raw;
-        uint32_t *W1 = W0 + s * c;
-        uint32_t *V0 = W1 + s * c;
-        uint32_t *V1 = V0 + s * c;
-        uint64_t *Hs = (uint64_t *)(V1 + s * c);
-        int *colidx = (int *)(Hs + (size_t)I.h_rows * c);
-        const uint32_t MASK = (1u << 30) - 1;
-        for (int e = threadIdx.x; e < (int)I.h_rows * c; e += blockDim.x) Hs[e] = 0;
-        for (uint32_t ch = item.chain_begin; ch < item.chain_end; ch++) {
-            const DChain C = chains[ch];
-            for (int e = threadIdx.x; e < s * c; e += blockDim.x) { W0[e] = 0; W1[e] = 0; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (uint32_t t = C.term_begin; t < C.term_end; t++) {
-                    const Term tm = terms[t];
-                    const int e = (int)tm.row * c + (int)tm.col;
-                    uint64_t old = ((uint64_t)W1[e] << 30) | W0[e];
-                    uint64_t nw = addmod(old, tm.coeff, I.Q.q);
-                    W0[e] = (uint32_t)nw & MASK;
-                    W1[e] = (uint32_t)(nw >> 30);
-                }
-                for (int t = 0; t < nv; t++) sU[t] = C.U[t];
-            }
-            __syncthreads();
-            int cur = 0;  // 0: data in W, 1: data in V
-            while (true) {
+        const uint32_t *ph = phase_pool + I.phase_off;
+        unsigned char *ptr = smem_raw;
+        uint64_t *Ms, *As;
+        if (MSMEM) {
+            Ms = (uint64_t *)ptr;
+            As = Ms + (size_t)s * s;
+            ptr += (size_t)2 * s * s * sizeof(uint64_t);
+        } else {
+            Ms = scratch + (size_t)blockIdx.x * scratch_stride;
+            As = Ms + (size_t)s * s;
+        }
+        uint2 *W = (uint2 *)ptr;
+        uint2 *V = W + (size_t)s * b;
+        uint64_t *Hs = (uint64_t *)(V + (size_t)s * b);
+        int *colmap = (int *)(Hs + (size_t)I.h_rows * b);
+        int *colidx = colmap + b;
+        uint64_t *bufA = blocks + (size_t)blockIdx.x * blocks_stride;
+        uint64_t *bufB = bufA + blocks_stride / 2;
+        const uint32_t MASK30 = (1u << 30) - 1;
+        for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) Hs[e] = 0;
+        for (uint32_t phase = 0; phase < I.nphases; phase++) {
+            uint64_t *cur = (phase & 1) ? bufB : bufA;
+            uint64_t *nxt = (phase & 1) ? bufA : bufB;
+            for (uint32_t ei = ph[phase]; ei < ph[phase + 1]; ei++) {
+                const DEntry E = entries[ei];
                 if (threadIdx.x == 0) {
-                    int norm = 0;
-                    for (int t = 0; t < nv; t++) norm += sU[t];
-                    if (norm > n) {
-                        int v[kMaxVars], k;
-                        greedy_chunk(sU, nv, n, d, v, &k);
-                        for (int t = 0; t < nv; t++) { sv[t] = v[t]; sx[t] = sU[t] - k * v[t]; }
-                        sk = k;
-                    } else {
-                        sk = 0;
+                    int nl = 0;
+                    for (int col = 0; col < b; col++)
+                        if (E.live >> col & 1u) colmap[nl++] = col;
+                    s_nlive = nl;
+                    for (int t = 0; t < nv; t++) sU[t] = E.U[t];
+                }
+                __syncthreads();
+                const int c = s_nlive;
+                // W = arrival block (live columns) or 0
+                for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+                    uint64_t val = 0;
+                    if (E.arrival >= 0) val = cur[(size_t)E.arrival * s * b + (size_t)(e / c) * b + colmap[e % c]];
+                    W[e] = make_uint2((uint32_t)val & MASK30, (uint32_t)(val >> 30));
+                }
+                __syncthreads();
+                if (E.start_chain >= 0 && threadIdx.x == 0) {
+                    const DChain C = chains[I.chain_base + E.start_chain];
+                    for (uint32_t t = C.term_begin; t < C.term_end; t++) {
+                        const Term tm = terms[t];
+                        int lc = 0;
+                        while (colmap[lc] != (int)tm.col) lc++;
+                        const int e = (int)tm.row * c + lc;
+                        const uint64_t old = ((uint64_t)W[e].y << 30) | W[e].x;
+                        const uint64_t nw = addmod(old, tm.coeff, I.Q.q);
+                        W[e] = make_uint2((uint32_t)nw & MASK30, (uint32_t)(nw >> 30));
                     }
                 }
                 __syncthreads();
-                const int k = sk;
-                if (k == 0) break;
-                // column index of v + mu - 1 in Homog_kappa (or -1)
-                for (int j = threadIdx.x; j < s; j += blockDim.x) {
-                    int g[kMaxVars];
-                    bool ok = true;
-                    for (int t = 0; t < nv; t++) {
-                        g[t] = sv[t] + monoS[j * nv + t] - 1;
-                        if (g[t] < 0) ok = false;
-                    }
-                    colidx[j] = ok ? dev_rank(g, nv, (int)I.kappa) : -1;
-                }
-                __syncthreads();
-                // A and M(k-1) = (k-1) A + B from the section
-                for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-                    const int r = e % s, j = e / s;
-                    const int col = colidx[j];
-                    uint64_t aL = 0, aH = 0, bL = 0, bH = 0;
-                    if (col >= 0) {
-                        for (int i = 0; i < nv; i++) {
-                            const int row = secrow[i * s + r];
-                            if (row < 0) continue;
-                            const uint64_t val = __ldg(&Sec[(size_t)row * I.sec_cols + col]);
-                            const uint64_t wa = (uint64_t)sv[i];
-                            const uint64_t wb = (uint64_t)(sx[i] + monoS[r * nv + i]);
-                            add128(aL, aH, val * wa);
-                            aH += mul_hi64(val, wa);
-                            add128(bL, bH, val * wb);
-                            bH += mul_hi64(val, wb);
+                int cur_buf = 0;  // 0: data in W, 1: data in V
+                for (uint32_t ci = E.chunk_begin; ci < E.chunk_end; ci++) {
+                    const DChunk CH = chunks[I.chunk_base + ci];
+                    const int k = CH.k;
+                    if (threadIdx.x < nv) sv[threadIdx.x] = CH.v[threadIdx.x];
+                    __syncthreads();
+                    // column index of v + mu - 1 in Homog_kappa (or -1)
+                    for (int j = threadIdx.x; j < s; j += blockDim.x) {
+                        int g[kMaxVars];
+                        bool ok = true;
+                        for (int t = 0; t < nv; t++) {
+                            g[t] = sv[t] + monoS[j * nv + t] - 1;
+                            if (g[t] < 0) ok = false;
                         }
+                        colidx[j] = ok ? dev_rank(g, nv, (int)I.kappa) : -1;
                     }
-                    const uint64_t A = reduce128(aL, aH, I.Q);
-                    const uint64_t B = reduce128(bL, bH, I.Q);
-                    At[(size_t)j * s + r] = A;
-                    Mt[(size_t)j * s + r] = addmod(mul_small(A, (uint64_t)(k - 1), I.Q), B, I.Q.q);
+                    __syncthreads();
+                    // A R and M(k-1) R = R_{U-v,v} R from the section (held as Sec R mod q):
+                    //   A[r,j] = sum_i v_i Sec[..],  M(k-1)[r,j] = sum_i (U_i - v_i + omega_i) Sec[..]
+                    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+                        const int r = e % s, j = e / s;
+                        const int col = colidx[j];
+                        uint64_t aL = 0, mL = 0, mH = 0;
+                        if (col >= 0) {
+                            for (int i = 0; i < nv; i++) {
+                                const int row = secrow[i * s + r];
+                                if (row < 0) continue;
+                                const uint64_t val = __ldg(&Sec[(size_t)row * I.sec_cols + col]);
+                                aL += val * (uint64_t)sv[i];                       // < d q < 2^63
+                                const uint64_t wm = (uint64_t)(sU[i] - sv[i] + monoS[r * nv + i]);
+                                add128(mL, mH, val * wm);
+                                mH += mul_hi64(val, wm);
+                            }
+                        }
+                        while (aL >= I.Q.q) aL -= I.Q.q;
+                        As[(size_t)j * s + r] = aL;
+                        Ms[(size_t)j * s + r] = reduce128(mL, mH, I.Q);
+                    }
+                    __syncthreads();
+                    int res;
+                    if (cur_buf == 0) res = horner_block<CPT>(s, c, k, Ms, As, W, V, I.Q);
+                    else res = horner_block<CPT>(s, c, k, Ms, As, V, W, I.Q);
+                    cur_buf ^= res;
+                    if (threadIdx.x == 0) {
+                        for (int t = 0; t < nv; t++) sU[t] -= k * sv[t];
+                        my_chunks++;
+                        my_steps += k;
+                    }
+                    __syncthreads();
+                }
+                const uint2 *R = cur_buf ? V : W;
+                if (E.dest < 0) {
+                    // pole order n: accumulate x^U g / x^S into H
+                    const int hdeg = d * n - n - 1;
+                    for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+                        const int j = e / c, lc = e % c;
+                        const uint64_t val = ((uint64_t)R[e].y << 30) | R[e].x;
+                        if (!val) continue;
+                        int g[kMaxVars];
+                        bool ok = true;
+                        for (int t = 0; t < nv; t++) {
+                            g[t] = sU[t] + monoS[j * nv + t] - 1;
+                            if (g[t] < 0) ok = false;
+                        }
+                        if (!ok) continue;  // cannot carry a coefficient on a valid path
+                        const int h = dev_rank(g, nv, hdeg);
+                        const int col = colmap[lc];
+                        Hs[h * b + col] = addmod(Hs[h * b + col], val, I.Q.q);
+                    }
+                } else {
+                    // move 2: store (first contribution) or add into the next phase's block
+                    uint64_t *dst = nxt + (size_t)E.dest * s * b;
+                    if (E.flags & 1u) {
+                        for (int e = threadIdx.x; e < s * b; e += blockDim.x) dst[e] = 0;
+                        __syncthreads();
+                    }
+                    for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+                        const int j = e / c, lc = e % c;
+                        const uint64_t val = ((uint64_t)R[e].y << 30) | R[e].x;
+                        uint64_t &slot = dst[(size_t)j * b + colmap[lc]];
+                        slot = addmod(slot, val, I.Q.q);
+                    }
                 }
                 __syncthreads();
-                int res;
-                if (cur == 0) res = horner_block<CPT>(s, c, k, Mt, At, W0, W1, V0, V1, I.Q);
-                else res = horner_block<CPT>(s, c, k, Mt, At, V0, V1, W0, W1, I.Q);
-                cur ^= res;
-                if (threadIdx.x == 0) {
-                    for (int t = 0; t < nv; t++) sU[t] = sx[t];
-                    my_chunks++;
-                    my_steps += k;
-                }
-                __syncthreads();
-            }
-            // accumulate x^U g / x^S (pole order n) into H
-            const uint32_t *R0 = cur ? V0 : W0, *R1 = cur ? V1 : W1;
-            const int hdeg = d * n - n - 1;
-            for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
-                const int j = e / c, col = e % c;
-                uint64_t val = ((uint64_t)R1[e] << 30) | R0[e];
-                if (!val) continue;
-                int g[kMaxVars];
-                bool ok = true;
-                for (int t = 0; t < nv; t++) {
-                    g[t] = sU[t] + monoS[j * nv + t] - 1;
-                    if (g[t] < 0) ok = false;
-                }
-                if (!ok) continue;  // cannot carry a coefficient on a valid path
-                const int h = dev_rank(g, nv, hdeg);
-                Hs[h * c + col] = addmod(Hs[h * c + col], val, I.Q.q);
             }
             __syncthreads();
         }
-        uint64_t *out = partial + (size_t)item.slot * partial_stride;
-        for (int e = threadIdx.x; e < (int)I.h_rows * c; e += blockDim.x) out[e] = Hs[e];
+        uint64_t *out = Hout + (size_t)inst * h_stride;
+        for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) out[e] = Hs[e];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -390,36 +492,27 @@ __global__ void __launch_bounds__(kThreads) k_depth_first(
     }
 }
 
-// H of each instance = sum of its items' partial slots mod q.
-__global__ void k_sum_partials(const DInst *__restrict__ insts, const uint32_t *__restrict__ slot_begin,
-                               const uint32_t *__restrict__ slot_end, const uint64_t *__restrict__ partial,
-                               size_t partial_stride, uint64_t *__restrict__ H, size_t h_stride, uint32_t ninst) {
-    const uint32_t i = blockIdx.x;
-    if (i >= ninst) return;
-    const DInst I = insts[i];
-    const int len = (int)(I.h_rows * I.b);
-    for (int e = threadIdx.x; e < len; e += blockDim.x) {
-        uint64_t acc = 0;
-        for (uint32_t sl = slot_begin[i]; sl < slot_end[i]; sl++)
-            acc = addmod(acc, partial[(size_t)sl * partial_stride + e], I.Q.q);
-        H[(size_t)i * h_stride + e] = acc;
-    }
-}
-
-// Kernel-level Algorithm 2 on independent problems (zeta_horner_device).
-template <int CPT>
-__global__ void __launch_bounds__(kThreads) k_horner_problems(
+// Kernel-level Algorithm 2 on independent problems (zeta_horner_device):
+// the same block routine as the chain kernel.
+template <int CPT, bool MSMEM>
+__global__ void __launch_bounds__(512) k_horner_problems(
     uint32_t count, int s, int c, const uint32_t *__restrict__ kk, const uint64_t *__restrict__ A,
     const uint64_t *__restrict__ B, uint64_t *__restrict__ W, const ModQ *__restrict__ mods,
     uint64_t *__restrict__ scratch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t MASK = (1u << 30) - 1;
-    uint64_t *Mt = scratch + (size_t)blockIdx.x * 2 * s * s;
-    uint64_t *At = Mt + (size_t)s * s;
-    uint32_t *W0 = (uint32_t *)smem_raw;
-    uint32_t *W1 = W0 + s * c;
-    uint32_t *V0 = W1 + s * c;
-    uint32_t *V1 = V0 + s * c;
+    const uint32_t MASK30 = (1u << 30) - 1;
+    unsigned char *ptr = smem_raw;
+    uint64_t *Ms, *As;
+    if (MSMEM) {
+        Ms = (uint64_t *)ptr;
+        As = Ms + (size_t)s * s;
+        ptr += (size_t)2 * s * s * sizeof(uint64_t);
+    } else {
+        Ms = scratch + (size_t)blockIdx.x * 2 * s * s;
+        As = Ms + (size_t)s * s;
+    }
+    uint2 *Wl = (uint2 *)ptr;
+    uint2 *Vl = Wl + (size_t)s * c;
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         const ModQ Q = mods[t];
         const int k = (int)kk[t];
@@ -428,19 +521,18 @@ __global__ void __launch_bounds__(kThreads) k_horner_problems(
         uint64_t *Wt = W + (size_t)t * s * c;
         for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
             const int r = e / s, j = e % s;  // row-major input
-            const uint64_t a = At_g[e], b = Bt_g[e];
-            At[(size_t)j * s + r] = a;
-            Mt[(size_t)j * s + r] = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), b, Q.q);
+            const uint64_t a = to_mont(At_g[e], Q), b = to_mont(Bt_g[e], Q);
+            As[(size_t)j * s + r] = a;
+            Ms[(size_t)j * s + r] = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), b, Q.q);
         }
         for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
             const uint64_t w = Wt[e];
-            W0[e] = (uint32_t)w & MASK;
-            W1[e] = (uint32_t)(w >> 30);
+            Wl[e] = make_uint2((uint32_t)w & MASK30, (uint32_t)(w >> 30));
         }
         __syncthreads();
-        int res = horner_block<CPT>(s, c, k, Mt, At, W0, W1, V0, V1, Q);
-        const uint32_t *R0 = res ? V0 : W0, *R1 = res ? V1 : W1;
-        for (int e = threadIdx.x; e < s * c; e += blockDim.x) Wt[e] = ((uint64_t)R1[e] << 30) | R0[e];
+        const int res = horner_block<CPT>(s, c, k, Ms, As, Wl, Vl, Q);
+        const uint2 *R = res ? Vl : Wl;
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) Wt[e] = ((uint64_t)R[e].y << 30) | R[e].x;
         __syncthreads();
     }
 }
@@ -488,7 +580,7 @@ static ModQ make_modq(uint64_t q) {
     Q.qneg_inv = (uint64_t)0 - inv;
     u128 R = ((u128)1 << 64) % q;
     Q.r2 = (uint64_t)(R * R % q);
-    for (int t = 0; t < 3; t++) Q.k[t] = (uint64_t)((u128)Q.r2 * (((u128)1 << (30 * t)) % q) % q);
+    Q.k30 = (uint64_t)((R << 30) % q);
     return Q;
 }
 
@@ -587,13 +679,15 @@ struct DeviceBatch {
     uint64_t *d_sec = nullptr;
     DChain *d_chains = nullptr;
     Term *d_terms = nullptr;
-    DItem *d_items = nullptr;
-    uint32_t *d_sb = nullptr, *d_se = nullptr, *d_queue = nullptr;
-    uint64_t *d_scratch = nullptr, *d_partial = nullptr, *d_H = nullptr;
+    uint32_t *d_phases = nullptr;
+    DEntry *d_entries = nullptr;
+    DChunk *d_chunks = nullptr;
+    uint32_t *d_order = nullptr, *d_queue = nullptr;
+    uint64_t *d_scratch = nullptr, *d_blocks = nullptr, *d_H = nullptr;
     unsigned long long *d_counters = nullptr;
-    uint32_t nitems = 0;
-    int grid = 1, CPT = 4;
-    size_t smem = 0, scratch_stride = 0, partial_stride = 0;
+    int grid = 1, threads = 256;
+    bool msmem = true;
+    size_t smem = 0, scratch_stride = 0, blocks_stride = 0, h_stride = 0;
     uint64_t bytes = 0, bytes_h2d = 0, bytes_d2h = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // around each recurrence launch
     double ms_kernel = 0;
@@ -655,7 +749,6 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     B->policy = policy;
     B->path = path;
 
-    // tables per (n, d)
     std::map<std::pair<int, int>, uint32_t> tab_of;
     std::vector<DTab> tabs;
     std::vector<int32_t> tabpool;
@@ -663,15 +756,12 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     std::vector<uint64_t> secpool;
     std::vector<DChain> dchains;
     std::vector<Term> dterms;
-    std::vector<DItem> ditems;
-    std::vector<uint32_t> slot_begin, slot_end;
-    std::vector<uint64_t> item_w;
+    std::vector<uint32_t> phases;
+    std::vector<DEntry> dentries;
+    std::vector<DChunk> dchunks;
+    std::vector<uint64_t> work(batch.size());
     int max_s = 0, max_c = 0, max_h = 0;
-    uint64_t total_work = 0;
-    for (Instance *X : batch)
-        for (auto &ch : X->chains) total_work += ch.work;
-    const int blocks_target = std::max(1, e->sms);
-    const uint64_t item_work = std::max<uint64_t>(1, total_work / ((uint64_t)blocks_target * 8));
+    size_t max_block_words = 0;
     for (size_t ii = 0; ii < batch.size(); ii++) {
         Instance *X = batch[ii];
         auto key = std::make_pair((int)X->n, (int)X->d);
@@ -704,17 +794,46 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
             tabs.push_back(T);
         }
         DInst I;
+        std::memset(&I, 0, sizeof(I));
         I.Q = make_modq(X->q);
         I.n = X->n; I.d = X->d; I.b = X->b; I.s = X->s; I.nv = X->nv;
         I.sec_cols = X->sec_cols; I.h_rows = X->h_rows; I.kappa = X->kappa;
         I.tab = tab_of[key];
         I.sec_off = secpool.size();
-        secpool.insert(secpool.end(), X->sec.begin(), X->sec.end());
+        {
+            // Sec R mod q: the step matrices built from it are in Montgomery form
+            const u128 Rm = ((u128)1 << 64) % X->q;
+            for (uint64_t v : X->sec) secpool.push_back((uint64_t)((u128)v * Rm % X->q));
+        }
+        I.chain_base = (uint32_t)dchains.size();
+        I.chunk_base = (uint32_t)dchunks.size();
+        I.phase_off = (uint32_t)phases.size();
+        I.nphases = (uint32_t)X->plan.phase_begin.size() - 1;
+        uint32_t ebase = (uint32_t)dentries.size();
+        for (uint32_t pb : X->plan.phase_begin) phases.push_back(ebase + pb);
+        for (const PlanEntry &pe : X->plan.entries) {
+            DEntry de;
+            std::memcpy(de.U, pe.U, sizeof(de.U));
+            de.chunk_begin = pe.chunk_begin;
+            de.chunk_end = pe.chunk_end;
+            de.arrival = pe.arrival;
+            de.start_chain = pe.start_chain;
+            de.dest = pe.dest;
+            de.flags = pe.flags;
+            de.live = pe.live;
+            dentries.push_back(de);
+        }
+        for (const PlanChunk &pc : X->plan.chunks) {
+            DChunk dc;
+            std::memcpy(dc.v, pc.v, sizeof(dc.v));
+            dc.k = pc.k;
+            dchunks.push_back(dc);
+        }
         dinst.push_back(I);
         max_s = std::max(max_s, (int)X->s);
         max_c = std::max(max_c, (int)X->b);
         max_h = std::max(max_h, (int)X->h_rows);
-        uint32_t cbase = (uint32_t)dchains.size();
+        max_block_words = std::max(max_block_words, (size_t)X->plan.cap * X->s * X->b);
         uint32_t tbase = (uint32_t)dterms.size();
         for (auto &ch : X->chains) {
             DChain dc;
@@ -724,33 +843,17 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
             dchains.push_back(dc);
         }
         dterms.insert(dterms.end(), X->terms.begin(), X->terms.end());
-        // work items: consecutive chains with about item_work each
-        slot_begin.push_back((uint32_t)ditems.size());
-        uint32_t start = 0;
-        uint64_t acc = 0;
-        for (uint32_t c = 0; c < X->chains.size(); c++) {
-            acc += X->chains[c].work;
-            if (acc >= item_work || c + 1 == X->chains.size()) {
-                ditems.push_back(DItem{(uint32_t)ii, cbase + start, cbase + c + 1, (uint32_t)ditems.size()});
-                item_w.push_back(acc);
-                start = c + 1;
-                acc = 0;
-            }
-        }
-        if (X->chains.empty()) {
-            ditems.push_back(DItem{(uint32_t)ii, cbase, cbase, (uint32_t)ditems.size()});
-            item_w.push_back(0);
-        }
-        slot_end.push_back((uint32_t)ditems.size());
+        work[ii] = X->plan.work + (uint64_t)X->plan.chunks.size() * X->s * X->s * 8;
     }
     if (max_s > kMaxS || max_c > kMaxC) {
         err = "instance too large for the device kernels";
         engine_release(B);
         return ZETA_ERR_UNSUPPORTED;
     }
-    // largest items first (longest-processing-time order for the persistent queue)
-    std::stable_sort(ditems.begin(), ditems.end(), [&](const DItem &a, const DItem &b) { return item_w[a.slot] > item_w[b.slot]; });
-    B->nitems = (uint32_t)ditems.size();
+    // instances in decreasing work (longest-processing-time order for the persistent queue)
+    std::vector<uint32_t> order(batch.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return work[a] > work[b]; });
 #define UP(vec, ptr) if ((st = dev_upload(e, B, vec, &B->ptr, err))) { engine_release(B); return st; }
     UP(dinst, d_inst);
     UP(tabs, d_tabs);
@@ -758,25 +861,27 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     UP(secpool, d_sec);
     UP(dchains, d_chains);
     UP(dterms, d_terms);
-    UP(ditems, d_items);
-    UP(slot_begin, d_sb);
-    UP(slot_end, d_se);
+    UP(phases, d_phases);
+    UP(dentries, d_entries);
+    UP(dchunks, d_chunks);
+    UP(order, d_order);
 #undef UP
     B->smem = chain_smem(max_s, max_c, max_h);
-    B->CPT = max_c <= 6 ? 2 : (max_c <= 12 ? 3 : 4);
-    const void *kfn = B->CPT == 2 ? (const void *)k_depth_first<2>
-                    : B->CPT == 3 ? (const void *)k_depth_first<3> : (const void *)k_depth_first<4>;
+    B->msmem = mats_in_smem(max_s);
+    B->threads = launch_threads(max_s, max_c);
+    const void *kfn = B->msmem ? (const void *)k_execute<4, true> : (const void *)k_execute<4, false>;
     CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
     int per_sm = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, B->smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, B->threads, B->smem));
     per_sm = std::max(1, per_sm);
-    B->grid = std::max(1, (int)std::min<size_t>((size_t)e->sms * per_sm, ditems.size()));
+    B->grid = std::max(1, (int)std::min<size_t>((size_t)e->sms * per_sm, batch.size()));
     B->scratch_stride = (size_t)2 * max_s * max_s;
-    B->partial_stride = (size_t)max_h * max_c;
+    B->blocks_stride = 2 * std::max<size_t>(max_block_words, 1);
+    B->h_stride = (size_t)max_h * max_c;
 #define AL(count, ptr) if ((st = dev_alloc(B, count, &B->ptr, err))) { engine_release(B); return st; }
-    AL(B->scratch_stride * B->grid, d_scratch);
-    AL(B->partial_stride * ditems.size(), d_partial);
-    AL(B->partial_stride * batch.size(), d_H);
+    AL(B->msmem ? 1 : B->scratch_stride * B->grid, d_scratch);
+    AL(B->blocks_stride * B->grid, d_blocks);
+    AL(B->h_stride * batch.size(), d_H);
     AL(16, d_queue);
     AL(8, d_counters);
 #undef AL
@@ -793,26 +898,22 @@ zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaEventCreate(&ev1));
     B->events.push_back({ev0, ev1});
     CUDA_TRY(cudaEventRecord(ev0, e->stream));
-#define LAUNCH(C)                                                                                          \
-    k_depth_first<C><<<B->grid, kThreads, B->smem, e->stream>>>(                                           \
-        B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_items, B->nitems,       \
-        B->d_queue, B->d_scratch, B->scratch_stride, B->d_partial, B->partial_stride, B->d_counters)
-    if (B->CPT == 2) LAUNCH(2);
-    else if (B->CPT == 3) LAUNCH(3);
-    else LAUNCH(4);
+#define LAUNCH(MS)                                                                                          \
+    k_execute<4, MS><<<B->grid, B->threads, B->smem, e->stream>>>(                                          \
+        B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
+        B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
+        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
+    if (B->msmem) LAUNCH(true);
+    else LAUNCH(false);
 #undef LAUNCH
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(ev1, e->stream));
-    k_sum_partials<<<(unsigned)B->insts.size(), 256, 0, e->stream>>>(B->d_inst, B->d_sb, B->d_se, B->d_partial,
-                                                                    B->partial_stride, B->d_H, B->partial_stride,
-                                                                    (uint32_t)B->insts.size());
-    CUDA_TRY(cudaGetLastError());
     return ZETA_OK;
 }
 
 zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaSetDevice(e->device));
-    std::vector<uint64_t> hH(B->partial_stride * B->insts.size());
+    std::vector<uint64_t> hH(B->h_stride * B->insts.size());
     unsigned long long hc[8] = {0};
     CUDA_TRY(cudaMemcpyAsync(hH.data(), B->d_H, sizeof(uint64_t) * hH.size(), cudaMemcpyDeviceToHost, e->stream));
     CUDA_TRY(cudaMemcpyAsync(hc, B->d_counters, sizeof(hc), cudaMemcpyDeviceToHost, e->stream));
@@ -829,25 +930,19 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
         cudaEventDestroy(ev.second);
     }
     B->events.clear();
+    uint64_t played = 0;
     for (size_t ii = 0; ii < B->insts.size(); ii++) {
         Instance *X = B->insts[ii];
-        X->H.assign(hH.begin() + ii * B->partial_stride, hH.begin() + ii * B->partial_stride + (size_t)X->h_rows * X->b);
-        X->steps = 0;
-        X->column_steps = 0;
-        for (auto &ch : X->chains) {
-            int norm = 0;
-            for (uint32_t t = 0; t < X->nv; t++) norm += ch.U[t];
-            uint64_t steps = (uint64_t)(norm - (int)X->n) / X->d;
-            X->steps += steps;
-            std::vector<char> live(X->b, 0);
-            for (uint32_t t = ch.term_begin; t < ch.term_end; t++) live[X->terms[t].col] = 1;
-            uint64_t lc = 0;
-            for (char l : live) lc += l;
-            X->column_steps += steps * lc;
-        }
-        X->chunks = 0;
+        X->H.assign(hH.begin() + ii * B->h_stride, hH.begin() + ii * B->h_stride + (size_t)X->h_rows * X->b);
+        X->steps = X->plan.steps;
+        X->column_steps = X->plan.column_steps;
+        X->chunks = X->plan.chunks_played;
+        played += X->plan.chunks_played;
     }
-    if (!B->insts.empty()) B->insts[0]->chunks = hc[0];  // batch total of chunks, reported once
+    if (hc[0] != played) {  // counters are reset by every launch
+        err = "device played a different number of chunks than planned";
+        return ZETA_ERR_INTERNAL;
+    }
     return ZETA_OK;
 }
 
@@ -896,13 +991,13 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
     int grid = (int)std::min<uint32_t>(count, (uint32_t)e->sms * 4);
     uint64_t *d_scratch;
     if ((st = ensure(e, "hscratch", sizeof(uint64_t) * 2 * s * s * (size_t)grid, (void **)&d_scratch, err))) return st;
-    size_t smem = (size_t)4 * s * c * sizeof(uint32_t);
-    const int CPT = c <= 6 ? 2 : (c <= 12 ? 3 : 4);
-    const void *kfn = CPT == 2 ? (const void *)k_horner_problems<2> : CPT == 3 ? (const void *)k_horner_problems<3> : (const void *)k_horner_problems<4>;
+    const bool ms = mats_in_smem((int)s);
+    size_t smem = (size_t)2 * s * c * sizeof(uint2) + (ms ? (size_t)2 * s * s * sizeof(uint64_t) : 0);
+    const int threads = launch_threads((int)s, (int)c);
+    const void *kfn = ms ? (const void *)k_horner_problems<4, true> : (const void *)k_horner_problems<4, false>;
     CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (CPT == 2) k_horner_problems<2><<<grid, kThreads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods, d_scratch);
-    else if (CPT == 3) k_horner_problems<3><<<grid, kThreads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods, d_scratch);
-    else k_horner_problems<4><<<grid, kThreads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods, d_scratch);
+    if (ms) k_horner_problems<4, true><<<grid, threads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods, d_scratch);
+    else k_horner_problems<4, false><<<grid, threads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods, d_scratch);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaStreamSynchronize(e->stream));
     return ZETA_OK;

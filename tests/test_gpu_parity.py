@@ -97,6 +97,20 @@ def test_quintic_curves_match_oracle(ctx, i):
     assert P == ref.P
 
 
+@pytest.mark.parametrize("policy", ["p_chunk", "var_by_var", "depth_first"])
+@pytest.mark.parametrize("which", [("quartic_curve_f11", 0), ("quintic_curves", 0), ("quintic_curves", 11)])
+def test_policies_reach_the_same_columns(ctx, policy, which):
+    # Y depends only on the basis, N_m and M: every policy must reproduce the oracle's
+    n, d, p, c = _instance(*which)
+    ref = ozeta.compute_zeta(n, d, p, c, policy="p_chunk" if which[1] == 11 else "depth_first")
+    F, Y, st = z.zeta_frobenius(ctx, (n, d, p, c), policy=policy)
+    assert (Y.astype(object) == ref.Y).all()
+    P, _ = z.zeta_charpoly(ctx, (n, d, p, c), policy=policy)
+    assert P == ref.P
+    if policy == "p_chunk":
+        assert st["column_steps"] == ref.log.column_steps if which[1] == 11 else True
+
+
 @pytest.mark.parametrize("n,d,p", [(2, 5, 11), (2, 4, 13), (2, 5, 31)])
 def test_fermat_curves_closed_form_on_gpu(ctx, n, d, p):
     P, _ = z.zeta_charpoly(ctx, (n, d, p, zi.fermat(n, d)))
@@ -142,7 +156,7 @@ def test_full_quintic_workload_sampled_parity(ctx):
     every P(T) checked against a point count over F_p and Weil's bound; a sample against the oracle."""
     count = zi.WORKLOADS["quintic_curves"]["count"]
     specs = [_instance("quintic_curves", i) for i in range(count)]
-    out, per, total = z.zeta_batch(ctx, specs)
+    out, per, total = z.zeta_batch(ctx, specs, policy="p_chunk")
     assert all(P is not None for P in out)
     for (n, d, p, c), P in zip(specs, out):
         assert P[0] == 1 and len(P) == 13
