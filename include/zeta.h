@@ -199,6 +199,34 @@ zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, ui
                                const uint32_t *k, const uint64_t *A, const uint64_t *B,
                                uint64_t *W, const uint64_t *q);
 
+/* Allocation-free form of zeta_horner_device, for callers that cannot
+ * allocate device memory: code running inside another framework's memory
+ * pool or a fixed memory budget, plugins that must not call cudaMalloc (or
+ * any allocating library routine) after start-up, and code that enqueues
+ * work while allocation is forbidden.  The paper has no counterpart; it
+ * computes exactly what zeta_horner_device computes (the same block routine
+ * for Algorithm 2), with the same arguments minus the context.
+ *  - Runs on the CURRENT device, on `cuda_stream` (NULL: legacy default
+ *    stream), and returns after the stream has drained.
+ *  - Scratch: the step matrices of the problems in flight live in one
+ *    file-scope device array of 16 MiB per device (2^21 uint64), which every
+ *    GPU that loads the library holds until the process exits.  Limits:
+ *    s <= 512, c <= 32, 2 s^2 <= 2^21 - 32 words (one problem's matrices),
+ *    2 s c * 8 bytes of shared memory <= 227 KB.  Larger sizes return
+ *    ZETA_ERR_ARG before anything is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents; the
+ *    matrices are fully written before they are read and the status word is
+ *    cleared at the start of each call.  Calls that overlap on the GPU (two
+ *    streams, two host threads) race on the array: serialise them.
+ *  - Allocates nothing: no cudaMalloc, cudaFree, host heap, or library
+ *    allocator.  ZETA_ERR_ARG also reports a modulus outside [3, 2^60] or
+ *    even (that problem's W is left unchanged). */
+zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uint32_t s, uint32_t c,
+                               const uint32_t *k, const uint64_t *A, const uint64_t *B,
+                               uint64_t *W, const uint64_t *q);
+
 /* ---------------------------------------------------------------------------
  * Host-only entry points (no device needed): the setup and finishing steps
  * of the path, exposed so that they can be checked in isolation.

@@ -26,7 +26,7 @@ STATUS = {0: "ZETA_OK", 1: "ZETA_ERR_ARG", 2: "ZETA_ERR_NOT_SMOOTH", 3: "ZETA_ER
 
 EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta_frobenius",
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
-           "zeta_batch_release", "zeta_horner_device", "zeta_plan", "zeta_finish"]
+           "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish"]
 FLAG_Y_ONLY = 1
 
 
@@ -95,6 +95,9 @@ def _load():
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_finish.argtypes = [P(Hypersurface), P(Options), ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p]
+    lib.zeta_horner_static.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]
     lib.zeta_batch_prepare.argtypes = [ctypes.c_void_p, P(Hypersurface), ctypes.c_size_t, P(Options),
                                        P(ctypes.c_void_p)]
     lib.zeta_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -345,3 +348,11 @@ def zeta_finish(spec, H, **opt):
     _check(None, LIB.zeta_finish(ctypes.byref(hs), ctypes.byref(o), H.ctypes.data, F.ctypes.data,
                                  Y.ctypes.data, buf.ctypes.data))
     return F, Y, [_coeff128(buf[2 * i], buf[2 * i + 1]) for i in range(b + 1)]
+
+
+def zeta_horner_static(stream, count, s, c, k, A, B, W, q):
+    """Allocation-free kernel-level Algorithm 2 on the current device (see include/zeta.h)."""
+    def ptr(x):
+        return x if isinstance(x, int) else x.data_ptr()
+    st = LIB.zeta_horner_static(stream, count, s, c, ptr(k), ptr(A), ptr(B), ptr(W), ptr(q))
+    _check(None, st)

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1003,4 +1004,125 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
     return ZETA_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the kernel-level entry point (zeta_horner_static).
+// Its matrix scratch lives in this file-scope device array; every call on a
+// device shares it.  The last 32 words hold the call's status flag.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchWords = (size_t)2 << 20;  // 2 Mi uint64 = 16 MiB per device
+constexpr size_t kStaticStatusWord = kStaticScratchWords - 32;
+static __device__ __align__(256) uint64_t g_static_scratch[kStaticScratchWords];
+
+// ModQ of q computed on the device (no host round trip): -q^{-1} mod 2^64 by
+// Newton iteration, 2^64 mod q as (2^64 - q) mod q, then modular doublings.
+__device__ ModQ modq_on_device(uint64_t q) {
+    ModQ Q;
+    Q.q = q;
+    uint64_t inv = 1;
+    for (int i = 0; i < 7; i++) inv *= 2 - q * inv;
+    Q.qneg_inv = (uint64_t)0 - inv;
+    const uint64_t r = ((uint64_t)0 - q) % q;  // 2^64 mod q
+    uint64_t r2 = r, k30 = r;
+    for (int i = 0; i < 64; i++) { r2 <<= 1; if (r2 >= q) r2 -= q; }   // 2^128 mod q
+    for (int i = 0; i < 30; i++) { k30 <<= 1; if (k30 >= q) k30 -= q; } // 2^30 2^64 mod q
+    Q.r2 = r2;
+    Q.k30 = k30;
+    return Q;
+}
+
+template <int CPT>
+__global__ void __launch_bounds__(512) k_horner_problems_static(
+    uint32_t count, int s, int c, const uint32_t *__restrict__ kk, const uint64_t *__restrict__ A,
+    const uint64_t *__restrict__ B, uint64_t *__restrict__ W, const uint64_t *__restrict__ qv,
+    uint64_t *__restrict__ scratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t MASK30 = (1u << 30) - 1;
+    uint64_t *Ms = scratch + (size_t)blockIdx.x * 2 * s * s;
+    uint64_t *As = Ms + (size_t)s * s;
+    uint2 *Wl = (uint2 *)smem_raw;
+    uint2 *Vl = Wl + (size_t)s * c;
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const uint64_t q = qv[t];
+        if (q < 3 || q > ((uint64_t)1 << 60) || !(q & 1) || (uint64_t)s >= 8 * q) {
+            if (threadIdx.x == 0) atomicOr((unsigned long long *)&scratch[kStaticStatusWord], 1ull);
+            continue;  // uniform across the block: W_t is left unchanged
+        }
+        const ModQ Q = modq_on_device(q);
+        const int k = (int)kk[t];
+        const uint64_t *At_g = A + (size_t)t * s * s;
+        const uint64_t *Bt_g = B + (size_t)t * s * s;
+        uint64_t *Wt = W + (size_t)t * s * c;
+        for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+            const int r = e / s, j = e % s;  // row-major input
+            const uint64_t a = to_mont(At_g[e], Q), b = to_mont(Bt_g[e], Q);
+            As[(size_t)j * s + r] = a;
+            Ms[(size_t)j * s + r] = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), b, Q.q);
+        }
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+            const uint64_t w = Wt[e];
+            Wl[e] = make_uint2((uint32_t)w & MASK30, (uint32_t)(w >> 30));
+        }
+        __syncthreads();
+        const int res = horner_block<CPT>(s, c, k, Ms, As, Wl, Vl, Q);
+        const uint2 *R = res ? Vl : Wl;
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) Wt[e] = ((uint64_t)R[e].y << 30) | R[e].x;
+        __syncthreads();
+    }
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+uint64_t *g_static_ptr[kMaxDevices];
+std::once_flag g_static_once[kMaxDevices];
+cudaError_t g_static_err[kMaxDevices];
+}  // namespace
+
+// Device address of g_static_scratch on the current device (set up once per device).
+static cudaError_t static_scratch(int dev, uint64_t **out) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(g_static_once[dev], [dev]() {
+        g_static_err[dev] = cudaGetSymbolAddress((void **)&g_static_ptr[dev], g_static_scratch);
+    });
+    *out = g_static_ptr[dev];
+    return g_static_err[dev];
+}
+
+}  // namespace zeta
+
+extern "C" zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uint32_t s, uint32_t c,
+                                          const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
+                                          const uint64_t *q) {
+    using namespace zeta;
+    if (count && (!k || !A || !B || !W || !q)) return ZETA_ERR_ARG;
+    if (s == 0 || c == 0 || s > (uint32_t)kMaxS || c > (uint32_t)kMaxC) return ZETA_ERR_ARG;
+    const size_t per_block = (size_t)2 * s * s;
+    if (per_block > kStaticStatusWord) return ZETA_ERR_ARG;
+    const size_t smem = (size_t)2 * s * c * sizeof(uint2);
+    if (smem > 227 * 1024) return ZETA_ERR_ARG;
+    if (count == 0) return ZETA_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return ZETA_ERR_DEVICE; }
+    uint64_t *scratch = nullptr;
+    if (static_scratch(dev, &scratch) != cudaSuccess || !scratch) { cudaGetLastError(); return ZETA_ERR_DEVICE; }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ZETA_ERR_DEVICE;
+    const size_t fit = kStaticStatusWord / per_block;
+    const int grid = (int)std::min<size_t>(std::min<size_t>(count, fit), (size_t)sms * 4);
+    const int threads = launch_threads((int)s, (int)c);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaFuncSetAttribute((const void *)k_horner_problems_static<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) { cudaGetLastError(); return ZETA_ERR_DEVICE; }
+    // the status word must start at zero for every call
+    if (cudaMemsetAsync(scratch + kStaticStatusWord, 0, sizeof(uint64_t), st) != cudaSuccess) return ZETA_ERR_DEVICE;
+    k_horner_problems_static<4><<<grid, threads, smem, st>>>(count, (int)s, (int)c, k, A, B, W, q, scratch);
+    if (cudaGetLastError() != cudaSuccess) return ZETA_ERR_DEVICE;
+    uint64_t flag = 0;
+    if (cudaMemcpyAsync(&flag, scratch + kStaticStatusWord, sizeof(flag), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ZETA_ERR_DEVICE;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return ZETA_ERR_DEVICE;
+    return flag ? ZETA_ERR_ARG : ZETA_OK;
+}
+
+namespace zeta {
 }  // namespace zeta
