@@ -248,8 +248,9 @@ def main():
     macs_per_launch = tot["column_steps"] * s * s
     achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # ALU peak: 152 SMs x 64 32-bit IMAD per clock / 4 IMAD.WIDE per modular MAC (30-bit limbs)
-    alu_peak = 152 * 64 / 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # ALU peak of the implemented arithmetic: 152 SMs x 64 mad.wide.u32 per SM per clock
+    # (a probe measured 59-63) / 6 mad.wide.u32 per modular multiply-add (20 x 30-bit limbs)
+    alu_peak = 152 * 64 / 6 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "zeta/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -265,7 +266,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": None,
                      "kernel": "k_depth_first", "ms_per_launch": ms_kernel,
-                     "peak_basis": "152 SM x 64 IMAD/clk / 4 IMAD.WIDE per 30-bit-limb modular MAC at %.0f MHz"
+                     "peak_basis": "152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
                                    % peaks.get("sm_max_mhz", 2070.0)},
         "clocks": clk,
         "host": {"ms_setup": tot_e2e["ms_host_setup"], "ms_finish": tot_e2e["ms_host_finish"],
