@@ -152,3 +152,24 @@ def test_exact_divisibility_fails_for_a_planted_mistake(quartic_f11):
     finally:
         zeta.frobenius_terms = orig
     assert caught
+
+
+def test_gauss_sum_formula_against_brute_force_counts():
+    # the closed form itself, checked by counting points of x^4 + y^4 + z^4 over F_13^r, r = 1..3
+    P = pins.fermat_charpoly(2, 4, 13)
+    counts = [pins.count_points(2, 4, 13, zi.fermat(2, 4), r) for r in (1, 2, 3)]
+    assert pins.charpoly_to_counts(2, 13, P, 3) == counts
+
+
+def test_hasse_witt_against_brute_force_counts():
+    # P(T) mod p from the Hasse-Witt matrix against P(T) determined by point counts (genus 3, F_7)
+    att = 0
+    while True:
+        c = zi.dense_candidate(2, 4, 7, 555, 0, att)
+        att += 1
+        if cohomology.is_smooth(2, 4, 7, c):
+            break
+    counts = [pins.count_points(2, 4, 7, c, r) for r in (1, 2, 3)]
+    a = pins.counts_to_charpoly_prefix(2, 7, counts)
+    hw = pins.hasse_witt_charpoly_mod_p(2, 4, 7, c)
+    assert [x % 7 for x in a] == hw
