@@ -265,7 +265,7 @@ def main():
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": None,
-                     "kernel": "k_depth_first", "ms_per_launch": ms_kernel,
+                     "kernel": "k_execute", "ms_per_launch": ms_kernel,
                      "peak_basis": "152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
                                    % peaks.get("sm_max_mhz", 2070.0)},
         "clocks": clk,

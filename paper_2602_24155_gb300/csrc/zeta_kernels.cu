@@ -131,14 +131,21 @@ __device__ __forceinline__ uint64_t to_mont(uint64_t a, const ModQ &Q) {
 //          [j*s + r] (shared memory for small s, global scratch otherwise);
 //          Ms holds M(k-1) R = ((k-1)A + B) R on entry and is consumed
 //          (M <- M - A).
-//  W, V  : s x c limb pairs in shared memory, [j*c + col]; the input is in
-//          W; the output is in the buffer returned (0 = W, 1 = V).
-// Thread item = (row r, group of CPT consecutive columns).
+//  W, V  : s x cs limb pairs in shared memory, [j*cs + col], cs = c rounded
+//          up to a multiple of 4 (the padding columns hold zeros and stay
+//          zero); the input is in W; the output is in the buffer returned
+//          (0 = W, 1 = V).
+// Thread item = (row r, group of 4 consecutive columns); W is read 16 bytes
+// (two columns) at a time.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int pad4(int c) { return (c + 3) & ~3; }
+
 template <int CPT>
 __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *As, uint2 *W, uint2 *V,
                             const ModQ &Q) {
-    const int ngroups = (c + CPT - 1) / CPT;
+    static_assert(CPT == 4, "items are groups of four columns");
+    const int cs = pad4(c);
+    const int ngroups = cs / 4;
     const int items = s * ngroups;
     const uint32_t MASK20 = (1u << 20) - 1, MASK30 = (1u << 30) - 1;
     int cur = 0;
@@ -147,61 +154,46 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
         uint2 *out = cur ? W : V;
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int r = it % s;
-            const int c0 = (it / s) * CPT;
-            const int nc = min(CPT, c - c0);
-            uint64_t S[CPT][6];
+            const int c0 = (it / s) * 4;
+            uint64_t S[4][6];
 #pragma unroll
-            for (int cc = 0; cc < CPT; cc++)
+            for (int cc = 0; cc < 4; cc++)
 #pragma unroll
                 for (int t = 0; t < 6; t++) S[cc][t] = 0;
-            const uint64_t *mcol = Ms + r;
-            const uint2 *wrow = in + c0;
-            if (nc == CPT) {
-                for (int j = 0; j < s; j++) {
-                    const uint64_t m = mcol[(size_t)j * s];
-                    const uint32_t m0 = (uint32_t)m & MASK20;
-                    const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
-                    const uint32_t m2 = (uint32_t)(m >> 40);
-                    const uint2 *wj = wrow + j * c;
-#pragma unroll
-                    for (int cc = 0; cc < CPT; cc++) {
-                        const uint2 w = wj[cc];
-                        madw(S[cc][0], m0, w.x);
-                        madw(S[cc][1], m0, w.y);
-                        madw(S[cc][2], m1, w.x);
-                        madw(S[cc][3], m1, w.y);
-                        madw(S[cc][4], m2, w.x);
-                        madw(S[cc][5], m2, w.y);
-                    }
-                }
-            } else {
-                for (int j = 0; j < s; j++) {
-                    const uint64_t m = mcol[(size_t)j * s];
-                    const uint32_t m0 = (uint32_t)m & MASK20;
-                    const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
-                    const uint32_t m2 = (uint32_t)(m >> 40);
-                    const uint2 *wj = wrow + j * c;
-#pragma unroll
-                    for (int cc = 0; cc < CPT; cc++) {
-                        if (cc < nc) {
-                            const uint2 w = wj[cc];
-                            madw(S[cc][0], m0, w.x);
-                            madw(S[cc][1], m0, w.y);
-                            madw(S[cc][2], m1, w.x);
-                            madw(S[cc][3], m1, w.y);
-                            madw(S[cc][4], m2, w.x);
-                            madw(S[cc][5], m2, w.y);
-                        }
-                    }
-                }
+            const uint64_t *mp = Ms + r;
+            const uint4 *wp = reinterpret_cast<const uint4 *>(in + c0);
+            const int wstride = cs / 2;  // uint4 per W row
+#pragma unroll 2
+            for (int j = 0; j < s; j++) {
+                const uint64_t m = *mp;
+                mp += s;
+                const uint32_t m0 = (uint32_t)m & MASK20;
+                const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
+                const uint32_t m2 = (uint32_t)(m >> 40);
+                const uint4 wa = wp[0], wb = wp[1];  // columns c0, c0+1 | c0+2, c0+3
+                wp += wstride;
+                madw(S[0][0], m0, wa.x); madw(S[0][1], m0, wa.y);
+                madw(S[0][2], m1, wa.x); madw(S[0][3], m1, wa.y);
+                madw(S[0][4], m2, wa.x); madw(S[0][5], m2, wa.y);
+                madw(S[1][0], m0, wa.z); madw(S[1][1], m0, wa.w);
+                madw(S[1][2], m1, wa.z); madw(S[1][3], m1, wa.w);
+                madw(S[1][4], m2, wa.z); madw(S[1][5], m2, wa.w);
+                madw(S[2][0], m0, wb.x); madw(S[2][1], m0, wb.y);
+                madw(S[2][2], m1, wb.x); madw(S[2][3], m1, wb.y);
+                madw(S[2][4], m2, wb.x); madw(S[2][5], m2, wb.y);
+                madw(S[3][0], m0, wb.z); madw(S[3][1], m0, wb.w);
+                madw(S[3][2], m1, wb.z); madw(S[3][3], m1, wb.w);
+                madw(S[3][4], m2, wb.z); madw(S[3][5], m2, wb.w);
             }
+            uint2 res[4];
 #pragma unroll
-            for (int cc = 0; cc < CPT; cc++) {
-                if (cc < nc) {
-                    const uint64_t v = fold_partials(S[cc], Q);
-                    out[r * c + c0 + cc] = make_uint2((uint32_t)v & MASK30, (uint32_t)(v >> 30));
-                }
+            for (int cc = 0; cc < 4; cc++) {
+                const uint64_t v = fold_partials(S[cc], Q);
+                res[cc] = make_uint2((uint32_t)v & MASK30, (uint32_t)(v >> 30));
             }
+            uint4 *o = reinterpret_cast<uint4 *>(out + r * cs + c0);
+            o[0] = make_uint4(res[0].x, res[0].y, res[1].x, res[1].y);
+            o[1] = make_uint4(res[2].x, res[2].y, res[3].x, res[3].y);
         }
         __syncthreads();
         if (step + 1 < k) {
@@ -294,7 +286,7 @@ __host__ __device__ inline bool mats_in_smem(int s) { return (size_t)2 * s * s *
 
 // Threads per block: one per (row, group of 4 columns) item, rounded to warps, 64..512.
 inline int launch_threads(int s, int c) {
-    int items = s * ((c + 3) / 4);
+    int items = s * (pad4(c) / 4);
     int t = ((items + 31) / 32) * 32;
     return std::max(64, std::min(512, t));
 }
@@ -304,7 +296,7 @@ inline int launch_threads(int s, int c) {
 __host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
     size_t bytes = 0;
     if (mats_in_smem(s)) bytes += (size_t)2 * s * s * sizeof(uint64_t);
-    bytes += (size_t)2 * s * c * sizeof(uint2);
+    bytes += (size_t)2 * s * pad4(c) * sizeof(uint2);
     bytes += (size_t)h_rows * c * sizeof(uint64_t);
     bytes += (size_t)(c + s) * sizeof(int) + 64;
     return bytes;
@@ -354,8 +346,8 @@ __global__ void __launch_bounds__(512) k_execute(
             As = Ms + (size_t)s * s;
         }
         uint2 *W = (uint2 *)ptr;
-        uint2 *V = W + (size_t)s * b;
-        uint64_t *Hs = (uint64_t *)(V + (size_t)s * b);
+        uint2 *V = W + (size_t)s * pad4(b);
+        uint64_t *Hs = (uint64_t *)(V + (size_t)s * pad4(b));
         int *colmap = (int *)(Hs + (size_t)I.h_rows * b);
         int *colidx = colmap + b;
         uint64_t *bufA = blocks + (size_t)blockIdx.x * blocks_stride;
@@ -376,10 +368,12 @@ __global__ void __launch_bounds__(512) k_execute(
                 }
                 __syncthreads();
                 const int c = s_nlive;
-                // W = arrival block (live columns) or 0
-                for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+                const int cs = pad4(c);
+                // W = arrival block (live columns) or 0; padding columns 0
+                for (int e = threadIdx.x; e < s * cs; e += blockDim.x) {
+                    const int j = e / cs, lc = e - j * cs;
                     uint64_t val = 0;
-                    if (E.arrival >= 0) val = cur[(size_t)E.arrival * s * b + (size_t)(e / c) * b + colmap[e % c]];
+                    if (E.arrival >= 0 && lc < c) val = cur[(size_t)E.arrival * s * b + (size_t)j * b + colmap[lc]];
                     W[e] = make_uint2((uint32_t)val & MASK30, (uint32_t)(val >> 30));
                 }
                 __syncthreads();
@@ -389,7 +383,7 @@ __global__ void __launch_bounds__(512) k_execute(
                         const Term tm = terms[t];
                         int lc = 0;
                         while (colmap[lc] != (int)tm.col) lc++;
-                        const int e = (int)tm.row * c + lc;
+                        const int e = (int)tm.row * cs + lc;
                         const uint64_t old = ((uint64_t)W[e].y << 30) | W[e].x;
                         const uint64_t nw = addmod(old, tm.coeff, I.Q.q);
                         W[e] = make_uint2((uint32_t)nw & MASK30, (uint32_t)(nw >> 30));
@@ -452,7 +446,7 @@ __global__ void __launch_bounds__(512) k_execute(
                     const int hdeg = d * n - n - 1;
                     for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
                         const int j = e / c, lc = e % c;
-                        const uint64_t val = ((uint64_t)R[e].y << 30) | R[e].x;
+                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << 30) | R[j * cs + lc].x;
                         if (!val) continue;
                         int g[kMaxVars];
                         bool ok = true;
@@ -474,7 +468,7 @@ __global__ void __launch_bounds__(512) k_execute(
                     }
                     for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
                         const int j = e / c, lc = e % c;
-                        const uint64_t val = ((uint64_t)R[e].y << 30) | R[e].x;
+                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << 30) | R[j * cs + lc].x;
                         uint64_t &slot = dst[(size_t)j * b + colmap[lc]];
                         slot = addmod(slot, val, I.Q.q);
                     }
@@ -513,7 +507,8 @@ __global__ void __launch_bounds__(512) k_horner_problems(
         As = Ms + (size_t)s * s;
     }
     uint2 *Wl = (uint2 *)ptr;
-    uint2 *Vl = Wl + (size_t)s * c;
+    uint2 *Vl = Wl + (size_t)s * pad4(c);
+    const int cs = pad4(c);
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         const ModQ Q = mods[t];
         const int k = (int)kk[t];
@@ -526,14 +521,18 @@ __global__ void __launch_bounds__(512) k_horner_problems(
             As[(size_t)j * s + r] = a;
             Ms[(size_t)j * s + r] = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), b, Q.q);
         }
-        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
-            const uint64_t w = Wt[e];
+        for (int e = threadIdx.x; e < s * cs; e += blockDim.x) {
+            const int j = e / cs, col = e - j * cs;
+            const uint64_t w = col < c ? Wt[j * c + col] : 0;
             Wl[e] = make_uint2((uint32_t)w & MASK30, (uint32_t)(w >> 30));
         }
         __syncthreads();
         const int res = horner_block<CPT>(s, c, k, Ms, As, Wl, Vl, Q);
         const uint2 *R = res ? Vl : Wl;
-        for (int e = threadIdx.x; e < s * c; e += blockDim.x) Wt[e] = ((uint64_t)R[e].y << 30) | R[e].x;
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+            const int j = e / c, col = e - j * c;
+            Wt[e] = ((uint64_t)R[j * cs + col].y << 30) | R[j * cs + col].x;
+        }
         __syncthreads();
     }
 }
@@ -993,7 +992,7 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
     uint64_t *d_scratch;
     if ((st = ensure(e, "hscratch", sizeof(uint64_t) * 2 * s * s * (size_t)grid, (void **)&d_scratch, err))) return st;
     const bool ms = mats_in_smem((int)s);
-    size_t smem = (size_t)2 * s * c * sizeof(uint2) + (ms ? (size_t)2 * s * s * sizeof(uint64_t) : 0);
+    size_t smem = (size_t)2 * s * pad4((int)c) * sizeof(uint2) + (ms ? (size_t)2 * s * s * sizeof(uint64_t) : 0);
     const int threads = launch_threads((int)s, (int)c);
     const void *kfn = ms ? (const void *)k_horner_problems<4, true> : (const void *)k_horner_problems<4, false>;
     CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1041,7 +1040,8 @@ __global__ void __launch_bounds__(512) k_horner_problems_static(
     uint64_t *Ms = scratch + (size_t)blockIdx.x * 2 * s * s;
     uint64_t *As = Ms + (size_t)s * s;
     uint2 *Wl = (uint2 *)smem_raw;
-    uint2 *Vl = Wl + (size_t)s * c;
+    uint2 *Vl = Wl + (size_t)s * pad4(c);
+    const int cs = pad4(c);
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         const uint64_t q = qv[t];
         if (q < 3 || q > ((uint64_t)1 << 60) || !(q & 1) || (uint64_t)s >= 8 * q) {
@@ -1059,14 +1059,18 @@ __global__ void __launch_bounds__(512) k_horner_problems_static(
             As[(size_t)j * s + r] = a;
             Ms[(size_t)j * s + r] = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), b, Q.q);
         }
-        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
-            const uint64_t w = Wt[e];
+        for (int e = threadIdx.x; e < s * cs; e += blockDim.x) {
+            const int j = e / cs, col = e - j * cs;
+            const uint64_t w = col < c ? Wt[j * c + col] : 0;
             Wl[e] = make_uint2((uint32_t)w & MASK30, (uint32_t)(w >> 30));
         }
         __syncthreads();
         const int res = horner_block<CPT>(s, c, k, Ms, As, Wl, Vl, Q);
         const uint2 *R = res ? Vl : Wl;
-        for (int e = threadIdx.x; e < s * c; e += blockDim.x) Wt[e] = ((uint64_t)R[e].y << 30) | R[e].x;
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+            const int j = e / c, col = e - j * c;
+            Wt[e] = ((uint64_t)R[j * cs + col].y << 30) | R[j * cs + col].x;
+        }
         __syncthreads();
     }
 }
@@ -1098,7 +1102,7 @@ extern "C" zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uin
     if (s == 0 || c == 0 || s > (uint32_t)kMaxS || c > (uint32_t)kMaxC) return ZETA_ERR_ARG;
     const size_t per_block = (size_t)2 * s * s;
     if (per_block > kStaticStatusWord) return ZETA_ERR_ARG;
-    const size_t smem = (size_t)2 * s * c * sizeof(uint2);
+    const size_t smem = (size_t)2 * s * pad4((int)c) * sizeof(uint2);
     if (smem > 227 * 1024) return ZETA_ERR_ARG;
     if (count == 0) return ZETA_OK;
     int dev = 0;
