@@ -28,6 +28,11 @@ sys.path.insert(0, ROOT)
 import zeta_inputs as zi  # noqa: E402
 
 METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
+
+# DRAM traffic of the executor from one ncu capture (profiles/k_execute_quintic_curves_456_full.md):
+# bytes read + written per instance of the quintic workload, valid for this kernel source only.
+PROFILED_KERNEL_MD5 = "f80003cbc8a0591ab02e0beb0ed19c5f"
+PROFILED_DRAM_BYTES_PER_INSTANCE = 6.91e9 / 456
 WORKLOAD = "quintic_curves"
 
 
@@ -244,6 +249,10 @@ def main():
 
     # roofline of the recurrence kernel: modular multiply-adds (s^2 per column step)
     peaks = _peaks()
+    import hashlib
+    src = os.path.join(ROOT, "paper_2602_24155_gb300", "csrc", "zeta_kernels.cu")
+    same_kernel = hashlib.md5(open(src, "rb").read()).hexdigest() == PROFILED_KERNEL_MD5
+    traffic = PROFILED_DRAM_BYTES_PER_INSTANCE * args.count if (same_kernel and args.policy == "p_chunk") else None
     ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
     macs_per_launch = tot["column_steps"] * s * s
     achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12
@@ -264,7 +273,7 @@ def main():
                 "d2h_bytes_per_step": tot_e2e["bytes_d2h"] + 16 * sum(len(P) for P in P_e2e)},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "k_execute", "ms_per_launch": ms_kernel,
                      "peak_basis": "152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
                                    % peaks.get("sm_max_mhz", 2070.0)},
