@@ -239,9 +239,17 @@ typedef struct {
     uint32_t r, M;
     uint64_t q;                 /* p^M */
     uint64_t nchains, nterms;
+    /* the reduction game played by opt->policy (Sec. 3.4) */
+    uint64_t plan_chunks;       /* move 1 count */
+    uint64_t plan_steps;        /* sum of chunk lengths */
+    uint64_t plan_column_steps; /* steps times carried columns */
+    uint64_t plan_merges;       /* move 2: duplicates combined */
+    uint64_t plan_entries;      /* terms processed over all phases */
+    uint64_t plan_cap;          /* largest number of merged terms waiting between two phases */
 } zeta_plan_info;
 
-/* Host setup of one instance (Sec. 2.3-2.5, Prop. 2.1, Alg. 1, Prop. 3.3):
+/* Host setup of one instance (Sec. 2.3-2.5, Prop. 2.1, Alg. 1, Prop. 3.3)
+ * and the reduction game of opt->policy (Sec. 3.4, Sec. 4), statistics in info:
  *  sec:        sec_rows x sec_cols uint64 (row-major) -- the section of the
  *              Jacobian map M_kappa over Z/q: column gamma holds g_0..g_n with
  *              sum_i g_i d_i f = x^gamma (rows (i, nu), nu in Homog_{n(d-2)}).

@@ -150,12 +150,14 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
                         u = sub_kv(u, v, k)
                         left -= k
                 nxt.append((u, w))
-            nxt = merge_terms(nxt, add, log)
+            # terms at pole order n leave the game (their numerators are summed
+            # by the final reduction); the others are combined
             done += [(u, w) for u, w in nxt if sum(u) == n]
-            live = [(u, w) for u, w in nxt if sum(u) > n]
+            live = merge_terms([(u, w) for u, w in nxt if sum(u) > n], add, log)
         return done
     if policy == "var_by_var":
         live = merge_terms(terms, add, log)
+        done = []
         for t in range(n, -1, -1):
             nxt = []
             for u, w in live:
@@ -166,8 +168,9 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
                     w = reduce_chunk(u, v, k, w)
                     u = sub_kv(u, v, k)
                 nxt.append((u, w))
-            live = merge_terms(nxt, add, log)
+            done += [(u, w) for u, w in nxt if sum(u) == n]
+            live = merge_terms([(u, w) for u, w in nxt if sum(u) > n], add, log)
         # after the u_0 phase every term has |u| = n
-        assert all(sum(u) == n for u, _ in live)
-        return live
+        assert not live
+        return done
     raise ValueError("unknown policy %r" % policy)

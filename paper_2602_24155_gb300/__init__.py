@@ -68,7 +68,10 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("b", ctypes.c_uint32), ("s", ctypes.c_uint32), ("nv", ctypes.c_uint32),
                 ("sec_rows", ctypes.c_uint32), ("sec_cols", ctypes.c_uint32), ("h_rows", ctypes.c_uint32),
                 ("r", ctypes.c_uint32), ("M", ctypes.c_uint32), ("q", ctypes.c_uint64),
-                ("nchains", ctypes.c_uint64), ("nterms", ctypes.c_uint64)]
+                ("nchains", ctypes.c_uint64), ("nterms", ctypes.c_uint64),
+                ("plan_chunks", ctypes.c_uint64), ("plan_steps", ctypes.c_uint64),
+                ("plan_column_steps", ctypes.c_uint64), ("plan_merges", ctypes.c_uint64),
+                ("plan_entries", ctypes.c_uint64), ("plan_cap", ctypes.c_uint64)]
 
 
 def _load():
@@ -333,7 +336,9 @@ def zeta_plan(spec, **opt):
     _check(None, LIB.zeta_plan(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(info), sec.ctypes.data,
                                U.ctypes.data, ct.ctypes.data, rc.ctypes.data, co.ctypes.data, fin.ctypes.data))
     return dict(b=info.b, s=info.s, nv=info.nv, r=info.r, M=info.M, q=info.q, h_rows=info.h_rows,
-                sec=sec, U=U, chain_terms=ct, term_rc=rc, term_coeff=co, fin=fin)
+                sec=sec, U=U, chain_terms=ct, term_rc=rc, term_coeff=co, fin=fin,
+                game=dict(chunks=info.plan_chunks, steps=info.plan_steps, column_steps=info.plan_column_steps,
+                          merges=info.plan_merges, entries=info.plan_entries, cap=info.plan_cap))
 
 
 def zeta_finish(spec, H, **opt):

@@ -280,8 +280,15 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
     zeta_options o = opt ? *opt : default_options();
     Instance X;
     zeta_status st = prepare_instance(hs, &o, true, X);
+    if (!st) st = schedule_policy(X, o.policy);
     if (st) return st;
     if (info) {
+        info->plan_chunks = X.plan.chunks_played;
+        info->plan_steps = X.plan.steps;
+        info->plan_column_steps = X.plan.column_steps;
+        info->plan_merges = X.plan.merges;
+        info->plan_entries = X.plan.entries.size();
+        info->plan_cap = X.plan.cap;
         info->b = X.b; info->s = X.s; info->nv = X.nv;
         info->sec_rows = X.sec_rows; info->sec_cols = X.sec_cols; info->h_rows = X.h_rows;
         info->r = X.r; info->M = X.M; info->q = X.q;

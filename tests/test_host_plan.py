@@ -112,3 +112,15 @@ def test_non_smooth_and_unsupported_inputs_are_rejected():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_query((2, 4, 11, [11] + [0] * 14))      # coefficient not reduced
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var"])
+@pytest.mark.parametrize("which", [("quartic_curve_f11", 0), ("quintic_curves", 0)])
+def test_host_game_matches_the_oracle_game(policy, which):
+    # the library's scheduler and the oracle's policies are separate code: same moves, same counts
+    n, d, p, c, _ = zi.draw_instance(*which, cohomology.is_smooth)
+    plan = z.zeta_plan((n, d, p, c), policy=policy)
+    res = ozeta.compute_zeta(n, d, p, c, policy=policy, want_P=False)
+    g = plan["game"]
+    assert (g["chunks"], g["steps"], g["merges"]) == (res.log.chunks, res.log.steps, res.log.merges)
+    assert g["column_steps"] >= res.log.column_steps
