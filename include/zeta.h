@@ -59,7 +59,9 @@ typedef enum {
 typedef enum {
     ZETA_POLICY_PCHUNK = 0,      /* Sec. 4.1: chunks of p on the terms of largest norm, then merge */
     ZETA_POLICY_DEPTH_FIRST = 1, /* Sec. 4.2: greedy v, largest chunk, never merge */
-    ZETA_POLICY_VAR_BY_VAR = 2   /* Sec. 4.3: clear u_n, merge, clear u_{n-1}, ... */
+    ZETA_POLICY_VAR_BY_VAR = 2,  /* Sec. 4.3: clear u_n, merge, clear u_{n-1}, ... */
+    ZETA_POLICY_LEARNED = 3      /* p-chunk whose chunk directions are proposed by a trained network
+                                    (zeta_options.policy_weights); Algorithm 3 if none is given */
 } zeta_policy;
 
 /* Which kernel runs the recurrence. */
@@ -84,6 +86,10 @@ typedef struct {
     uint32_t r_override;
     uint32_t N_override[8];
     uint32_t flags;             /* ZETA_FLAG_* bits */
+    /* ZETA_POLICY_LEARNED: host pointer to the network's float weights
+     * (layout of zeta_mlp_train) and its hidden width; NULL = Algorithm 3. */
+    const float *policy_weights;
+    uint32_t policy_hidden;
 } zeta_options;
 
 /* Stop after the unnormalised columns Y (no division by p^(v-m+1), no
@@ -226,6 +232,58 @@ zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, ui
 zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uint32_t s, uint32_t c,
                                const uint32_t *k, const uint64_t *A, const uint64_t *B,
                                uint64_t *W, const uint64_t *q);
+
+/* ---------------------------------------------------------------------------
+ * Learned reduction policy (ZETA_POLICY_LEARNED).  The paper closes Sec. 4
+ * noting that its policies never inspect U; this network proposes the
+ * direction of every chunk of every p-chunk (Sec. 4.1), seeing how many other
+ * terms reach each candidate's destination.  Any proposal gives the same
+ * Frobenius matrix: only the cost of the reduction game (Sec. 3.4) changes.
+ *
+ * Network: a candidate (u, v) is a row of ZETA_POLICY_FEATURES floats; score =
+ * w3 . relu(W2^T relu(W1^T x + b1) + b2) + b3 with hidden width H (1..128).
+ * Parameters, float, in this order: W1 (F x H, row-major), b1 (H), W2 (H x H),
+ * b2 (H), w3 (H), b3 (1).  A decision is a group of consecutive rows; the loss
+ * is the mean over groups of -log softmax(scores of the group)[label].
+ * Buffers are host buffers owned by the caller.
+ * ------------------------------------------------------------------------- */
+#define ZETA_POLICY_FEATURES 17
+
+/* Number of floats of the parameter vector for hidden width H. */
+size_t zeta_mlp_param_count(uint32_t hidden);
+
+/* Glorot-uniform initial weights from a seeded splitmix64 stream (host only). */
+zeta_status zeta_mlp_init(uint32_t hidden, uint64_t seed, float *params);
+
+/* Scores of n rows (GPU forward kernel). */
+zeta_status zeta_mlp_forward(zeta_ctx *ctx, uint32_t hidden, const float *params, const float *X, size_t n,
+                             float *scores);
+
+/* Loss and its gradient with respect to every parameter over all groups
+ * (GPU forward and backward kernels); group_off has ngroups+1 row offsets,
+ * labels[g] indexes the chosen row of group g. */
+zeta_status zeta_mlp_grad(zeta_ctx *ctx, uint32_t hidden, const float *params, const float *X,
+                          const uint32_t *group_off, const uint32_t *labels, size_t ngroups, float *grad,
+                          float *loss);
+
+/* Adam on mini-batches of batch_groups consecutive groups for `epochs` passes;
+ * params updated in place; final_loss (may be NULL) = mean batch loss of the
+ * last epoch. */
+zeta_status zeta_mlp_train(zeta_ctx *ctx, uint32_t hidden, float *params, const float *X,
+                           const uint32_t *group_off, const uint32_t *labels, size_t ngroups, uint32_t epochs,
+                           uint32_t batch_groups, float lr, float *final_loss);
+
+/* Training decisions of one instance, generated by the game itself (host
+ * only): the p-chunk game is played with a teacher rule (the legal direction
+ * with the longest chunk, ties to the smallest exponent reached), which
+ * combines more terms than Algorithm 3; every chunk decision with two or more
+ * legal directions is a group of candidate rows (row 0: Algorithm 3's choice)
+ * labelled with the teacher's choice; costs[row] = the teacher's chunk length
+ * minus the row's.  Two calls: with NULL buffers to read ngroups and ncand,
+ * then with buffers of ncand * ZETA_POLICY_FEATURES floats, ngroups+1 offsets,
+ * ngroups labels, ncand costs. */
+zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options *opt, size_t *ngroups,
+                                size_t *ncand, float *X, uint32_t *group_off, uint32_t *labels, int32_t *costs);
 
 /* ---------------------------------------------------------------------------
  * Host-only entry points (no device needed): the setup and finishing steps

@@ -17,7 +17,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libzeta.so")
 
-POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2}
+POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2, "learned": 3}
+POLICY_FEATURES = 17
 PATH = {"vector": 0, "gemm": 1}
 
 STATUS = {0: "ZETA_OK", 1: "ZETA_ERR_ARG", 2: "ZETA_ERR_NOT_SMOOTH", 3: "ZETA_ERR_UNSUPPORTED",
@@ -26,7 +27,9 @@ STATUS = {0: "ZETA_OK", 1: "ZETA_ERR_ARG", 2: "ZETA_ERR_NOT_SMOOTH", 3: "ZETA_ER
 
 EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta_frobenius",
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
-           "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish"]
+           "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
+           "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
+           "zeta_policy_dataset"]
 FLAG_Y_ONLY = 1
 
 
@@ -43,7 +46,8 @@ class Hypersurface(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("path", ctypes.c_int), ("r_override", ctypes.c_uint32),
-                ("N_override", ctypes.c_uint32 * 8), ("flags", ctypes.c_uint32)]
+                ("N_override", ctypes.c_uint32 * 8), ("flags", ctypes.c_uint32),
+                ("policy_weights", ctypes.POINTER(ctypes.c_float)), ("policy_hidden", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -101,6 +105,18 @@ def _load():
     lib.zeta_horner_static.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p]
+    lib.zeta_mlp_param_count.argtypes = [ctypes.c_uint32]
+    lib.zeta_mlp_init.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]
+    lib.zeta_mlp_forward.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]
+    lib.zeta_mlp_grad.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+    lib.zeta_mlp_train.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                   ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p]
+    lib.zeta_policy_dataset.argtypes = [P(Hypersurface), P(Options), P(ctypes.c_size_t), P(ctypes.c_size_t),
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_batch_prepare.argtypes = [ctypes.c_void_p, P(Hypersurface), ctypes.c_size_t, P(Options),
                                        P(ctypes.c_void_p)]
     lib.zeta_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
@@ -110,6 +126,7 @@ def _load():
     for name in EXPORTS:
         if name != "zeta_last_error":
             getattr(lib, name).restype = ctypes.c_int
+    lib.zeta_mlp_param_count.restype = ctypes.c_size_t
     return lib
 
 
@@ -126,9 +143,14 @@ class _Lazy:
 LIB = _Lazy()
 
 
-def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False):
+def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0):
     o = Options()
     o.flags = FLAG_Y_ONLY if y_only else 0
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        o.policy_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        o.policy_hidden = hidden
+        o._keep = w
     o.policy = POLICY[policy]
     o.path = PATH[path]
     o.r_override = r or 0
@@ -361,3 +383,63 @@ def zeta_horner_static(stream, count, s, c, k, A, B, W, q):
         return x if isinstance(x, int) else x.data_ptr()
     st = LIB.zeta_horner_static(stream, count, s, c, ptr(k), ptr(A), ptr(B), ptr(W), ptr(q))
     _check(None, st)
+
+
+# ---------------------------------------------------------------------------
+# Learned policy: network and training data (include/zeta.h)
+# ---------------------------------------------------------------------------
+def zeta_mlp_param_count(hidden):
+    return LIB.zeta_mlp_param_count(hidden)
+
+
+def zeta_mlp_init(hidden, seed):
+    w = np.zeros(zeta_mlp_param_count(hidden), dtype=np.float32)
+    _check(None, LIB.zeta_mlp_init(hidden, seed, w.ctypes.data))
+    return w
+
+
+def zeta_mlp_forward(ctx, hidden, params, X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    out = np.zeros(X.shape[0], dtype=np.float32)
+    _check(ctx, LIB.zeta_mlp_forward(ctx, hidden, params.ctypes.data, X.ctypes.data, X.shape[0], out.ctypes.data))
+    return out
+
+
+def zeta_mlp_grad(ctx, hidden, params, X, group_off, labels):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    go = np.ascontiguousarray(group_off, dtype=np.uint32)
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    grad = np.zeros_like(params)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(ctx, LIB.zeta_mlp_grad(ctx, hidden, params.ctypes.data, X.ctypes.data, go.ctypes.data, lab.ctypes.data,
+                                  len(lab), grad.ctypes.data, loss.ctypes.data))
+    return grad, float(loss[0])
+
+
+def zeta_mlp_train(ctx, hidden, params, X, group_off, labels, epochs, batch_groups, lr):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    p = np.array(params, dtype=np.float32, copy=True)
+    go = np.ascontiguousarray(group_off, dtype=np.uint32)
+    lab = np.ascontiguousarray(labels, dtype=np.uint32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(ctx, LIB.zeta_mlp_train(ctx, hidden, p.ctypes.data, X.ctypes.data, go.ctypes.data, lab.ctypes.data,
+                                   len(lab), epochs, batch_groups, lr, loss.ctypes.data))
+    return p, float(loss[0])
+
+
+def zeta_policy_dataset(spec, **opt):
+    """Training decisions of one instance: (X, group_off, labels, costs)."""
+    hs = _hypersurface(spec)
+    o = _options(**opt)
+    ng, nc = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(None, LIB.zeta_policy_dataset(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(ng), ctypes.byref(nc),
+                                         None, None, None, None))
+    X = np.zeros((nc.value, POLICY_FEATURES), dtype=np.float32)
+    go = np.zeros(ng.value + 1, dtype=np.uint32)
+    lab = np.zeros(ng.value, dtype=np.uint32)
+    cost = np.zeros(nc.value, dtype=np.int32)
+    _check(None, LIB.zeta_policy_dataset(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(ng), ctypes.byref(nc),
+                                         X.ctypes.data, go.ctypes.data, lab.ctypes.data, cost.ctypes.data))
+    return X, go, lab, cost

@@ -116,6 +116,8 @@ static zeta_status run_one(zeta_ctx *ctx, const zeta_hypersurface *hs, const zet
                            double *ms_dev) {
     zeta_options o = opt ? *opt : default_options();
     zeta_status st = prepare_instance(hs, &o, true, X);
+    X.net.w = o.policy_weights;
+    X.net.hidden = (int)o.policy_hidden;
     if (!st) st = schedule_policy(X, o.policy);
     if (st) { ctx->error = X.error; return st; }
     std::vector<Instance *> batch{&X};
@@ -180,6 +182,8 @@ zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_
     P->inst.resize(count);
     double t0 = now_ms();
     parallel_for(count, ctx->threads, [&](size_t i) {
+        P->inst[i].net.w = P->opt.policy_weights;
+        P->inst[i].net.hidden = (int)P->opt.policy_hidden;
         if (prepare_instance(&hs[i], &P->opt, true, P->inst[i]) == ZETA_OK) schedule_policy(P->inst[i], P->opt.policy);
     });
     for (auto &X : P->inst)
@@ -279,6 +283,8 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
     if (!hs) return ZETA_ERR_ARG;
     zeta_options o = opt ? *opt : default_options();
     Instance X;
+    X.net.w = o.policy_weights;
+    X.net.hidden = (int)o.policy_hidden;
     zeta_status st = prepare_instance(hs, &o, true, X);
     if (!st) st = schedule_policy(X, o.policy);
     if (st) return st;
@@ -305,6 +311,27 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
         if (term_coeff) term_coeff[t] = X.terms[t].coeff;
     }
     if (fin) std::memcpy(fin, X.fin.data(), sizeof(uint64_t) * X.fin.size());
+    return ZETA_OK;
+}
+
+zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options *opt, size_t *ngroups, size_t *ncand,
+                                float *X, uint32_t *group_off, uint32_t *labels, int32_t *costs) {
+    if (!hs || !ngroups || !ncand) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance I;
+    zeta_status st = prepare_instance(hs, &o, true, I);
+    if (st) return st;
+    std::vector<float> feat;
+    std::vector<uint32_t> goff, lab;
+    std::vector<int32_t> cost;
+    st = policy_dataset(I, feat, goff, lab, cost);
+    if (st) return st;
+    *ngroups = lab.size();
+    *ncand = cost.size();
+    if (X) std::memcpy(X, feat.data(), sizeof(float) * feat.size());
+    if (group_off) std::memcpy(group_off, goff.data(), sizeof(uint32_t) * goff.size());
+    if (labels) std::memcpy(labels, lab.data(), sizeof(uint32_t) * lab.size());
+    if (costs) std::memcpy(costs, cost.data(), sizeof(int32_t) * cost.size());
     return ZETA_OK;
 }
 

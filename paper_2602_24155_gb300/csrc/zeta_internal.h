@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/zeta.h"
@@ -59,6 +60,13 @@ struct Plan {
     uint64_t chunks_played = 0, steps = 0, column_steps = 0, merges = 0, work = 0;
 };
 
+// Learned direction policy (zeta_learn.cpp).
+constexpr int kPolicyFeatures = 17;
+struct PolicyNet {
+    const float *w = nullptr;  // W1 (F x H), b1 (H), W2 (H x H), b2 (H), w3 (H), b3 (1)
+    int hidden = 0;
+};
+
 struct Instance {
     // input
     uint32_t n = 0, d = 0, p = 0, nv = 0;
@@ -81,6 +89,10 @@ struct Instance {
     std::vector<Term> terms;
     std::vector<uint64_t> fin;   // b x h_rows final reduction map mod q
     Plan plan;
+    PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
+    // per level t: exponent -> terms reaching it in the p-chunk game with Algorithm 3
+    std::vector<std::unordered_map<uint64_t, int>> ref_contrib;
+    bool teacher = false;       // p-chunk played with teacher_direction (training data)
     // results
     std::vector<uint64_t> H;     // h_rows x b accumulated numerators mod q
     std::vector<uint64_t> Y;     // b x b
@@ -99,6 +111,18 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
 zeta_status finish_instance(Instance &X);
 // Plays the policy on the start chains of X and fills X.plan (zeta_policy.cpp).
 zeta_status schedule_policy(Instance &X, zeta_policy policy);
+
+size_t policy_param_count(int hidden);
+// Chooses the direction of a chunk of the p-chunk of the term at U (level t of tmax,
+// `left` steps left); false when no network is set or only one direction is legal.
+bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int tmax, int *v);
+// The rule that labels the training decisions: the legal direction with the longest chunk
+// (ties: the smallest exponent reached, descending lexicographic order).
+bool teacher_direction(const Instance &X, const int32_t *U, int left, int *v);
+zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<uint32_t> &group_off,
+                           std::vector<uint32_t> &labels, std::vector<int32_t> &costs);
+// Plays the p-chunk game with Algorithm 3 and records, per level, how many terms reach each exponent.
+zeta_status reference_contributions(Instance &X);
 zeta_status finish_y_only(Instance &X);  // Y = Fin * H only
 
 // Device engine (zeta_kernels.cu): runs the recurrence for every chain of

@@ -1,0 +1,296 @@
+// Learned direction policy for the reduction game (arXiv 2602.24155,
+// Sec. 3.4; Sec. 4.4 notes that the paper's policies never inspect U and
+// that better policies are open).  Inside every p-chunk (Sec. 4.1) the network
+// scores the legal directions v of each chunk and the best one is played; any
+// choice yields the same cohomology classes, only the game's cost changes.
+//
+// Training data comes from the game itself: the p-chunk game is played with a
+// teacher rule (the legal direction with the longest chunk, ties to the
+// smallest exponent reached), which combines more terms than Algorithm 3; every
+// chunk decision with two or more legal directions becomes a group of
+// candidates labelled with the teacher's choice.
+//
+// Features of a candidate (u, v), with w the exponent reached at the end of the
+// p-chunk (v first, then Algorithm 3):
+//   u_i/|u|, v_i/d, w_i/|w| for four coordinates (zero-padded),
+//   k/left (this chunk's length over the steps left), t/tmax (level),
+//   [v is Algorithm 3's choice],
+//   and what the policy sees of U: the number c of other terms that reach w in
+//   the p-chunk game played with Algorithm 3, as min(c, 4)/4 and [c > 0].
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "zeta_internal.h"
+
+namespace zeta {
+
+namespace {
+
+int norm(const int32_t *U, int nv) {
+    int s = 0;
+    for (int t = 0; t < nv; t++) s += U[t];
+    return s;
+}
+
+uint64_t pack(const int32_t *U, int nv) {
+    uint64_t key = 0;
+    for (int t = 0; t < nv; t++) key = (key << 12) | (uint64_t)U[t];
+    return key;
+}
+
+void greedy_dir(const int32_t *U, int nv, int d, int *v) {
+    int i = d;
+    for (int t = 0; t < nv; t++) v[t] = 0;
+    for (int t = 0; t < nv && i > 0; t++)
+        if (U[t] != 0) { v[t] = 1; i--; }
+    while (i > 0)
+        for (int t = 0; t < nv && i > 0; t++)
+            if (v[t] < U[t]) { v[t]++; i--; }
+}
+
+int kmax(const int32_t *U, const int *v, int nv, int n, int d) {
+    int k = (norm(U, nv) - n) / d;
+    for (int t = 0; t < nv; t++)
+        if (v[t] > 0) k = std::min(k, U[t] / v[t]);
+    return k;
+}
+
+// All v with |v| = d, v <= U, U_i != 0 => v_i >= 1 (Sec. 3.4, V_full) and k_max >= 1,
+// Algorithm 3's choice first.
+void legal_dirs(const int32_t *U, int nv, int n, int d, std::vector<std::array<int, kMaxVars>> &out) {
+    out.clear();
+    int g[kMaxVars];
+    greedy_dir(U, nv, d, g);
+    std::array<int, kMaxVars> ga{};
+    for (int t = 0; t < nv; t++) ga[t] = g[t];
+    out.push_back(ga);
+    std::array<int, kMaxVars> v{};
+    std::function<void(int, int)> rec = [&](int pos, int rem) {
+        if (pos == nv - 1) {
+            v[pos] = rem;
+            for (int t = 0; t < nv; t++) {
+                if (v[t] > U[t]) return;
+                if (U[t] != 0 && v[t] == 0) return;
+            }
+            if (kmax(U, v.data(), nv, n, d) < 1) return;
+            if (v == ga) return;
+            out.push_back(v);
+            return;
+        }
+        for (int x = 0; x <= rem; x++) {
+            v[pos] = x;
+            rec(pos + 1, rem - x);
+        }
+    };
+    rec(0, d);
+}
+
+// Exponent reached after `left` steps: first chunk in direction v, then Algorithm 3.
+void p_chunk_dest(const int32_t *U, const int *v, int left, int nv, int n, int d, int32_t *W, int *k_first) {
+    for (int t = 0; t < nv; t++) W[t] = U[t];
+    bool first = true;
+    *k_first = 0;
+    while (left > 0 && norm(W, nv) > n) {
+        int dir[kMaxVars];
+        if (first) for (int t = 0; t < nv; t++) dir[t] = v[t];
+        else greedy_dir(W, nv, d, dir);
+        int k = std::min(left, kmax(W, dir, nv, n, d));
+        if (k <= 0) break;
+        if (first) *k_first = k;
+        first = false;
+        for (int t = 0; t < nv; t++) W[t] -= k * dir[t];
+        left -= k;
+    }
+}
+
+void features(const int32_t *U, const int *v, const int32_t *W, int k_first, int left, int t, int tmax, int nv, int d,
+              bool is_greedy, int others, float *f) {
+    const float nu = (float)std::max(1, norm(U, nv)), nw = (float)std::max(1, norm(W, nv));
+    for (int i = 0; i < 4; i++) {
+        f[i] = i < nv ? U[i] / nu : 0.f;
+        f[4 + i] = i < nv ? (float)v[i] / d : 0.f;
+        f[8 + i] = i < nv ? W[i] / nw : 0.f;
+    }
+    f[12] = left > 0 ? (float)k_first / left : 0.f;
+    f[13] = tmax > 0 ? (float)t / tmax : 0.f;
+    f[14] = is_greedy ? 1.f : 0.f;
+    f[15] = (float)std::min(std::max(others, 0), 4) / 4.f;
+    f[16] = others > 0 ? 1.f : 0.f;
+}
+
+// Other terms of the reference game that reach W at level t - 1, for the term at U
+// (its own Algorithm 3 destination `own` is not counted).
+int others_at(const Instance &X, int t, const int32_t *W, uint64_t own) {
+    if (t - 1 < 1 || t - 1 >= (int)X.ref_contrib.size()) return 0;
+    const uint64_t key = pack(W, (int)X.nv);
+    auto it = X.ref_contrib[t - 1].find(key);
+    int c = it == X.ref_contrib[t - 1].end() ? 0 : it->second;
+    return key == own ? c - 1 : c;
+}
+
+float mlp_score(const PolicyNet &net, const float *x) {
+    const int F = kPolicyFeatures, H = net.hidden;
+    const float *W1 = net.w, *b1 = W1 + F * H, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H, *b3 = w3 + H;
+    float h1[512], h2[512];
+    for (int j = 0; j < H; j++) {
+        float a = b1[j];
+        for (int i = 0; i < F; i++) a += x[i] * W1[i * H + j];
+        h1[j] = a > 0.f ? a : 0.f;
+    }
+    float out = b3[0];
+    for (int j = 0; j < H; j++) {
+        float a = b2[j];
+        for (int i = 0; i < H; i++) a += h1[i] * W2[i * H + j];
+        h2[j] = a > 0.f ? a : 0.f;
+        out += h2[j] * w3[j];
+    }
+    return out;
+}
+
+}  // namespace
+
+size_t policy_param_count(int hidden) {
+    const size_t F = kPolicyFeatures, H = hidden;
+    return F * H + H + H * H + H + H + 1;
+}
+
+bool teacher_direction(const Instance &X, const int32_t *U, int left, int *v) {
+    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
+    std::vector<std::array<int, kMaxVars>> cand;
+    legal_dirs(U, nv, n, d, cand);
+    if (cand.size() < 2) return false;
+    size_t arg = 0;
+    int bestk = -1;
+    std::array<int32_t, kMaxVars> bestw{};
+    for (size_t c = 0; c < cand.size(); c++) {
+        const int k = std::min(left, kmax(U, cand[c].data(), nv, n, d));
+        std::array<int32_t, kMaxVars> w{};
+        for (int t = 0; t < nv; t++) w[t] = U[t] - k * cand[c][t];
+        if (k > bestk || (k == bestk && w < bestw)) {
+            bestk = k;
+            bestw = w;
+            arg = c;
+        }
+    }
+    for (int q = 0; q < nv; q++) v[q] = cand[arg][q];
+    return true;
+}
+
+bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int tmax, int *v) {
+    if (!X.net.w || X.net.hidden <= 0 || X.net.hidden > 512 || X.nv > 4) return false;
+    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
+    std::vector<std::array<int, kMaxVars>> cand;
+    legal_dirs(U, nv, n, d, cand);
+    if (cand.size() < 2) return false;
+    int32_t own_w[kMaxVars];
+    int kf0;
+    p_chunk_dest(U, cand[0].data(), left, nv, n, d, own_w, &kf0);
+    const uint64_t own = pack(own_w, nv);
+    float best = -INFINITY;
+    size_t arg = 0;
+    for (size_t c = 0; c < cand.size(); c++) {
+        int32_t W[kMaxVars];
+        int kf;
+        p_chunk_dest(U, cand[c].data(), left, nv, n, d, W, &kf);
+        float f[kPolicyFeatures];
+        features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own), f);
+        float sc = mlp_score(X.net, f);
+        if (sc > best) { best = sc; arg = c; }
+    }
+    for (int q = 0; q < nv; q++) v[q] = cand[arg][q];
+    return true;
+}
+
+zeta_status reference_contributions(Instance &X) {
+    zeta_status st = schedule_policy(X, ZETA_POLICY_PCHUNK);
+    if (st) return st;
+    const int nv = (int)X.nv;
+    const Plan &P = X.plan;
+    const int nph = (int)P.phase_begin.size() - 1;
+    const int tmax = nph;  // phase i plays level tmax - i
+    X.ref_contrib.assign(tmax + 1, {});
+    for (int ph = 0; ph + 1 < nph; ph++) {
+        const int tn = tmax - ph - 1;  // next level
+        std::vector<uint64_t> block_key;
+        for (uint32_t e = P.phase_begin[ph + 1]; e < P.phase_begin[ph + 2]; e++) {
+            const PlanEntry &E = P.entries[e];
+            const uint64_t key = pack(E.U, nv);
+            if (E.start_chain >= 0) X.ref_contrib[tn][key] += 1;
+            if (E.arrival >= 0) {
+                if ((int)block_key.size() <= E.arrival) block_key.resize(E.arrival + 1, 0);
+                block_key[E.arrival] = key;
+            }
+        }
+        for (uint32_t e = P.phase_begin[ph]; e < P.phase_begin[ph + 1]; e++)
+            if (P.entries[e].dest >= 0) X.ref_contrib[tn][block_key[P.entries[e].dest]] += 1;
+    }
+    return ZETA_OK;
+}
+
+// Decisions of the p-chunk game played by the teacher rule (see the file comment):
+// every chunk decision with two or more legal directions, labelled with the
+// teacher's choice; costs[row] = the teacher's chunk length minus the row's
+// (0 for the label).
+zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<uint32_t> &group_off,
+                           std::vector<uint32_t> &labels, std::vector<int32_t> &costs) {
+    if (X.nv > 4) { X.error = "the policy features cover at most four variables"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    zeta_status st = reference_contributions(X);  // what the network sees of U
+    if (st) return st;
+    X.teacher = true;
+    st = schedule_policy(X, ZETA_POLICY_PCHUNK);
+    X.teacher = false;
+    if (st) return st;
+    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p;
+    const Plan &P = X.plan;
+    const int nph = (int)P.phase_begin.size() - 1;
+    const int tmax = nph;  // phase i plays level tmax - i
+    group_off.assign(1, 0);
+    std::vector<std::array<int, kMaxVars>> cand;
+    for (int ph = 0; ph < nph; ph++) {
+        const int t = tmax - ph;
+        for (uint32_t e = P.phase_begin[ph]; e < P.phase_begin[ph + 1]; e++) {
+            const PlanEntry &E = P.entries[e];
+            int32_t U[kMaxVars];
+            std::memcpy(U, E.U, sizeof(U));
+            int left = (t >= 2) ? p : p - n;
+            for (uint32_t ci = E.chunk_begin; ci < E.chunk_end; ci++) {
+                const PlanChunk &CH = P.chunks[ci];
+                legal_dirs(U, nv, n, d, cand);
+                if (cand.size() >= 2) {
+                    int32_t own_w[kMaxVars];
+                    int kf0;
+                    p_chunk_dest(U, cand[0].data(), left, nv, n, d, own_w, &kf0);
+                    const uint64_t own = pack(own_w, nv);
+                    uint32_t lab = 0;
+                    bool found = false;
+                    for (size_t c = 0; c < cand.size(); c++) {
+                        int32_t W[kMaxVars];
+                        int kf;
+                        p_chunk_dest(U, cand[c].data(), left, nv, n, d, W, &kf);
+                        float f[kPolicyFeatures];
+                        features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own), f);
+                        feat.insert(feat.end(), f, f + kPolicyFeatures);
+                        costs.push_back(CH.k - std::min(left, kmax(U, cand[c].data(), nv, n, d)));
+                        bool same = true;
+                        for (int q = 0; q < nv; q++) same &= cand[c][q] == CH.v[q];
+                        if (same) { lab = (uint32_t)c; found = true; }
+                    }
+                    if (!found) { X.error = "teacher move not among the legal directions"; return X.status = ZETA_ERR_INTERNAL; }
+                    labels.push_back(lab);
+                    group_off.push_back((uint32_t)(feat.size() / kPolicyFeatures));
+                }
+                for (int q = 0; q < nv; q++) U[q] -= CH.k * CH.v[q];
+                left -= CH.k;
+            }
+        }
+    }
+    return ZETA_OK;
+}
+
+}  // namespace zeta

@@ -15,6 +15,7 @@
 //               chunks until u_t = 0 (or pole order n), then combines.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <unordered_map>
 
 #include "zeta_internal.h"
@@ -56,13 +57,16 @@ uint64_t pack(const int32_t *U, int nv) {
 }
 
 // Greedy chunks from U until `stop` says so; appends to plan.chunks; U updated.
+// first (optional): direction of the first chunk instead of Algorithm 3.
+// choose (optional): proposes the direction of a chunk (U, steps left) instead of Algorithm 3.
 template <typename Stop>
-void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_steps) {
+void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_steps,
+                 const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
     const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
     int left = max_steps;
     while (norm(U, nv) > n && left > 0 && !stop(U)) {
         int v[kMaxVars];
-        greedy_v(U, nv, d, v);
+        if (!(choose && choose(U, left, v))) greedy_v(U, nv, d, v);
         int k = std::min(k_max(U, v, nv, n, d), left);
         if (k <= 0) break;
         PlanChunk c;
@@ -125,7 +129,8 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     struct Arr { int32_t block; uint32_t live; };
     std::unordered_map<uint64_t, Arr> cur, nxt;
     std::vector<std::vector<int32_t>> curU, nxtU;  // exponents of arrival blocks by index
-    auto phase = [&](const std::vector<int> &starts, auto stop_for, auto max_steps) {
+    auto phase = [&](const std::vector<int> &starts, auto stop_for, auto max_steps,
+                     const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
         // entries: arrivals of this phase, then start chains (merged into an arrival if equal u)
         P.phase_begin.push_back((uint32_t)P.entries.size());
         std::unordered_map<uint64_t, size_t> entry_of;
@@ -162,7 +167,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
             int32_t U[kMaxVars];
             std::memcpy(U, e.U, sizeof(U));
             e.chunk_begin = (uint32_t)P.chunks.size();
-            play_chunks(X, U, e.live, stop_for, max_steps(e));
+            play_chunks(X, U, e.live, stop_for, max_steps(e), choose);
             e.chunk_end = (uint32_t)P.chunks.size();
             if (norm(U, nv) == n) {
                 e.dest = -1;
@@ -187,7 +192,13 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
         curU.swap(nxtU);
     };
 
-    if (policy == ZETA_POLICY_PCHUNK) {
+    if (policy == ZETA_POLICY_LEARNED && X.net.w) {
+        // the network sees the terms of the p-chunk game played with Algorithm 3
+        zeta_status st = reference_contributions(X);
+        if (st) return st;
+        X.plan = Plan();
+    }
+    if (policy == ZETA_POLICY_PCHUNK || policy == ZETA_POLICY_LEARNED) {
         int tmax = 0;
         std::vector<std::vector<int>> by_level;
         for (size_t c = 0; c < X.chains.size(); c++) {
@@ -199,11 +210,16 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
             tmax = std::max(tmax, t);
         }
         for (int t = tmax; t >= 1; t--) {
-            const int K = p * t;
             const int steps = (t >= 2) ? p : p - n;  // to pole order p(t-1), or to n
-            (void)K;
+            std::function<bool(const int32_t *, int, int *)> choose = nullptr;
+            if (policy == ZETA_POLICY_LEARNED)
+                choose = [&X, t, tmax](const int32_t *U, int left, int *v) {
+                    return learned_direction(X, U, left, t, tmax, v);
+                };
+            else if (X.teacher)
+                choose = [&X](const int32_t *U, int left, int *v) { return teacher_direction(X, U, left, v); };
             phase(t < (int)by_level.size() ? by_level[t] : std::vector<int>(),
-                  [](const int32_t *) { return false; }, [&](const PlanEntry &) { return steps; });
+                  [](const int32_t *) { return false; }, [&](const PlanEntry &) { return steps; }, choose);
         }
     } else if (policy == ZETA_POLICY_VAR_BY_VAR) {
         std::vector<int> all(X.chains.size());

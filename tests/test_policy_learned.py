@@ -1,0 +1,95 @@
+"""Learned direction policy: the network's gradients against a float64 oracle, the training
+data generated by the game, and the gain of the trained network over Algorithm 3."""
+import numpy as np
+import pytest
+
+import zeta_inputs as zi
+from oracle import cohomology, mlp as omlp, zeta as ozeta
+
+z = pytest.importorskip("paper_2602_24155_gb300")
+
+
+def _instance(workload, i):
+    n, d, p, c, _ = zi.draw_instance(workload, i, cohomology.is_smooth)
+    return n, d, p, c
+
+
+def test_oracle_network_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    H = 8
+    P = omlp.F * H + H + H * H + H + H + 1
+    params = rng.normal(0, 0.5, P)
+    X = rng.normal(0, 1, (11, omlp.F))
+    go = np.array([0, 3, 7, 11])
+    lab = np.array([1, 0, 3])
+    loss, grad = omlp.loss_and_grad(params, H, X, go, lab)
+    eps = 1e-6
+    for k in rng.choice(P, 25, replace=False):
+        e = np.zeros(P)
+        e[k] = eps
+        num = (omlp.loss_and_grad(params + e, H, X, go, lab)[0] - omlp.loss_and_grad(params - e, H, X, go, lab)[0]) / (2 * eps)
+        assert abs(num - grad[k]) < 1e-6 * max(1.0, abs(num))
+
+
+def test_dataset_is_generated_by_the_game():
+    spec = _instance("quintic_curves", 0)
+    X, go, lab, cost = z.zeta_policy_dataset(spec)
+    assert X.shape[1] == z.POLICY_FEATURES and len(go) == len(lab) + 1
+    for g in range(len(lab)):
+        a, b = go[g], go[g + 1]
+        assert b - a >= 2
+        assert X[a, 14] == 1.0 and (X[a + 1:b, 14] == 0.0).all()   # row 0 is Algorithm 3's choice
+        assert cost[a + lab[g]] == 0 and (cost[a:b] >= 0).all()       # the teacher takes a longest chunk
+        assert ((X[a:b, 16] == 1.0) == (X[a:b, 15] > 0)).all()        # merge indicator agrees with the count
+
+
+def test_learned_policy_without_weights_plays_p_chunk():
+    spec = _instance("quintic_curves", 3)
+    a = z.zeta_plan(spec, policy="p_chunk")["game"]
+    b = z.zeta_plan(spec, policy="learned")["game"]
+    assert a == b
+
+
+@pytest.mark.gpu
+def test_gpu_network_gradient_matches_oracle():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    ctx = z.zeta_create(0)
+    try:
+        spec = _instance("quintic_curves", 1)
+        X, go, lab, _ = z.zeta_policy_dataset(spec)
+        X, go, lab = X[:go[200]], go[:201], lab[:200]
+        for H in (16, 64):
+            w = z.zeta_mlp_init(H, 7)
+            g, loss = z.zeta_mlp_grad(ctx, H, w, X, go, lab)
+            ref_loss, ref_g = omlp.loss_and_grad(w.astype(np.float64), H, X.astype(np.float64), go, lab)
+            assert abs(loss - ref_loss) < 1e-4 * max(1, abs(ref_loss))
+            assert np.allclose(g, ref_g, rtol=1e-3, atol=1e-5)
+            s = z.zeta_mlp_forward(ctx, H, w, X)
+            assert np.allclose(s, omlp.forward(w, H, X)[0], rtol=1e-4, atol=1e-5)
+    finally:
+        z.zeta_destroy(ctx)
+
+
+@pytest.mark.gpu
+def test_trained_policy_gains_over_algorithm_3_with_the_same_result():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_24155_gb300.policy_train import train_policy
+    ctx = z.zeta_create(0)
+    try:
+        train = [_instance("quintic_curves", i) for i in range(12, 12 + 48)]
+        held = [_instance("quintic_curves", i) for i in range(12)]
+        w, loss, nd = train_policy(ctx, train, hidden=64, epochs=30)
+        assert nd > 1000 and loss < 0.5
+        base = sum(z.zeta_plan(s, policy="p_chunk")["game"]["column_steps"] for s in held)
+        learned = sum(z.zeta_plan(s, policy="learned", weights=w, hidden=64)["game"]["column_steps"] for s in held)
+        assert learned < base, (learned, base)
+        for s in held[:3]:
+            P0, _ = z.zeta_charpoly(ctx, s, policy="p_chunk")
+            P1, _ = z.zeta_charpoly(ctx, s, policy="learned", weights=w, hidden=64)
+            assert P0 == P1
+    finally:
+        z.zeta_destroy(ctx)
