@@ -54,8 +54,8 @@ def _instances(rank, count):
     return out
 
 
-def _instances_lib(rank, count, z):
-    """Same instances, accepted by the library's own smoothness test."""
+def _instances_range(start, count, z):
+    """Instances start .. start+count-1, accepted by the library's own smoothness test."""
     def accept(n, d, p, c):
         try:
             z.zeta_query((n, d, p, c))
@@ -64,7 +64,11 @@ def _instances_lib(rank, count, z):
             if e.status == 2:
                 return False
             raise
-    return [zi.draw_instance(WORKLOAD, i, accept)[:4] for i in range(rank * count, rank * count + count)]
+    return [zi.draw_instance(WORKLOAD, i, accept)[:4] for i in range(start, start + count)]
+
+
+def _instances_lib(rank, count, z):
+    return _instances_range(rank * count, count, z)
 
 
 class Clocks:
@@ -174,7 +178,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--policy", default="p_chunk")
+    ap.add_argument("--policy", default="learned",
+                    help="learned (trained here on instances disjoint from the batch), p_chunk, depth_first, var_by_var")
+    ap.add_argument("--train-count", type=int, default=96)
     ap.add_argument("--path", default="vector")
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,6 +203,16 @@ def main():
     ctx = z.zeta_create(local, stream.cuda_stream)
     specs = _instances_lib(rank, args.count, z)
     opt = dict(policy=args.policy, path=args.path)
+    learned = None
+    if args.policy == "learned":
+        # training instances: the same workload recipe, indices past every rank's batch
+        from paper_2602_24155_gb300.policy_train import train_policy
+        train = _instances_range(world * args.count, args.train_count, z)
+        t0 = time.perf_counter()
+        weights, train_loss, decisions = train_policy(ctx, train, hidden=8, epochs=30)
+        learned = {"train_s": time.perf_counter() - t0, "decisions": decisions, "loss": train_loss,
+                   "hidden": 8, "train_instances": len(train)}
+        opt.update(weights=weights, hidden=8)
 
     # device-resident inputs: prepare once, then time the kernels
     plan = z.zeta_batch_prepare(ctx, specs, **opt)
@@ -235,6 +251,26 @@ def main():
     column_steps = tot["column_steps"] * world
     s = per[0]["s"]
 
+    # the plain policy of the paper on the same batch, for the learned-vs-plain comparison
+    policies = {args.policy: {"zeta_per_s": value, "column_steps": column_steps, "ms_per_step": ms_per_step}}
+    if learned is not None:
+        policies["learned"].update(learned)
+        plan2 = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", path=args.path)
+        plan2.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan2.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        P_plain, _, tot_plain = plan2.finish()
+        plan2.release()
+        assert P_plain == P_warm, "policies disagree"
+        ms_plain = e0.elapsed_time(e1)
+        policies["p_chunk"] = {"zeta_per_s": args.count / (ms_plain / 1000.0), "column_steps": tot_plain["column_steps"],
+                               "ms_per_step": ms_plain}
+
     # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -271,7 +307,8 @@ def main():
                    "column_steps_per_step": column_steps},
         "e2e": {"value": e2e_value, "unit": "zeta/s", "h2d_bytes_per_step": coeff_bytes + tot_e2e["bytes_h2d"],
                 "d2h_bytes_per_step": tot_e2e["bytes_d2h"] + 16 * sum(len(P) for P in P_e2e)},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
+        "policies": policies,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "k_execute", "ms_per_launch": ms_kernel,

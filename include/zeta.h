@@ -163,7 +163,9 @@ zeta_status zeta_frobenius(zeta_ctx *ctx, const zeta_hypersurface *hs, const zet
 zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt,
                           int64_t *P_out, zeta_stats *st);
 
-/* Many hypersurfaces (any mix of n, d, p) in one device pass.
+/* Many hypersurfaces (any mix of n, d, p).  Batches of 256 or more are split
+ * into four sub-batches whose host setup overlaps the device work of the
+ * previous one (one device pass each).
  *  P_out: count * stride * 2 int64; instance i writes b_i+1 coefficients
  *         (two words each, as in zeta_charpoly) at P_out + 2*i*stride
  *         (stride >= max b_i + 1).

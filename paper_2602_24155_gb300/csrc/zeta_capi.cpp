@@ -261,12 +261,38 @@ zeta_status zeta_batch_release(zeta_batch_plan *P) {
 zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
                        int64_t *P_out, size_t stride, zeta_stats *per_instance, zeta_stats *total) {
     if (!ctx || (!hs && count) || (!P_out && count)) return ZETA_ERR_ARG;
-    zeta_batch_plan *P = nullptr;
-    zeta_status st = zeta_batch_prepare(ctx, hs, count, opt, &P);
-    if (st) return st;
-    st = zeta_batch_run(ctx, P);
-    if (!st) st = zeta_batch_finish(ctx, P, P_out, stride, per_instance, total);
-    zeta_batch_release(P);
+    // Pipelined: the host setup of sub-batch i+1 runs while the GPU reduces
+    // sub-batch i (kernel launches are asynchronous on the context stream).
+    const size_t S = count >= 256 ? 4 : 1;
+    std::vector<zeta_batch_plan *> plans(S, nullptr);
+    zeta_status st = ZETA_OK;
+    for (size_t i = 0; i < S && !st; i++) {
+        const size_t a = count * i / S, b = count * (i + 1) / S;
+        st = zeta_batch_prepare(ctx, hs + a, b - a, opt, &plans[i]);
+        if (!st) st = zeta_batch_run(ctx, plans[i]);
+    }
+    zeta_stats agg;
+    std::memset(&agg, 0, sizeof(agg));
+    for (size_t i = 0; i < S && !st; i++) {
+        const size_t a = count * i / S, b = count * (i + 1) / S;
+        zeta_stats part;
+        st = zeta_batch_finish(ctx, plans[i], P_out + 2 * a * stride, stride, per_instance ? per_instance + a : nullptr,
+                               &part);
+        if (st) break;
+        agg.chains += part.chains;
+        agg.terms += part.terms;
+        agg.chunks += part.chunks;
+        agg.steps += part.steps;
+        agg.column_steps += part.column_steps;
+        agg.ms_host_setup += part.ms_host_setup;
+        agg.ms_host_finish += part.ms_host_finish;
+        agg.ms_kernel += part.ms_kernel;
+        agg.kernel_launches += part.kernel_launches;
+        agg.bytes_h2d += part.bytes_h2d;
+        agg.bytes_d2h += part.bytes_d2h;
+    }
+    for (auto *P : plans) zeta_batch_release(P);
+    if (!st && total) *total = agg;
     return st;
 }
 

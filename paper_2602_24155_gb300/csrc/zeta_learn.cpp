@@ -62,7 +62,7 @@ int kmax(const int32_t *U, const int *v, int nv, int n, int d) {
 }
 
 // All v with |v| = d, v <= U, U_i != 0 => v_i >= 1 (Sec. 3.4, V_full) and k_max >= 1,
-// Algorithm 3's choice first.
+// Algorithm 3's choice first; compositions of d enumerated with an explicit stack.
 void legal_dirs(const int32_t *U, int nv, int n, int d, std::vector<std::array<int, kMaxVars>> &out) {
     out.clear();
     int g[kMaxVars];
@@ -71,24 +71,33 @@ void legal_dirs(const int32_t *U, int nv, int n, int d, std::vector<std::array<i
     for (int t = 0; t < nv; t++) ga[t] = g[t];
     out.push_back(ga);
     std::array<int, kMaxVars> v{};
-    std::function<void(int, int)> rec = [&](int pos, int rem) {
+    int lo[kMaxVars], hi[kMaxVars];
+    for (int t = 0; t < nv; t++) {
+        lo[t] = U[t] != 0 ? 1 : 0;
+        hi[t] = std::min<int>(U[t], d);
+    }
+    // odometer over v_0..v_{nv-2}; v_{nv-1} = d - (sum of the others)
+    int pos = 0, rem = d;
+    v[0] = lo[0] - 1;
+    while (pos >= 0) {
         if (pos == nv - 1) {
             v[pos] = rem;
-            for (int t = 0; t < nv; t++) {
-                if (v[t] > U[t]) return;
-                if (U[t] != 0 && v[t] == 0) return;
-            }
-            if (kmax(U, v.data(), nv, n, d) < 1) return;
-            if (v == ga) return;
-            out.push_back(v);
-            return;
+            if (rem >= lo[pos] && rem <= hi[pos] && kmax(U, v.data(), nv, n, d) >= 1 && v != ga) out.push_back(v);
+            pos--;
+            continue;
         }
-        for (int x = 0; x <= rem; x++) {
-            v[pos] = x;
-            rec(pos + 1, rem - x);
+        // next value of v[pos]
+        if (v[pos] >= lo[pos]) rem += v[pos];
+        v[pos]++;
+        if (v[pos] > hi[pos] || v[pos] > rem) {
+            v[pos] = lo[pos] - 1;
+            pos--;
+            continue;
         }
-    };
-    rec(0, d);
+        rem -= v[pos];
+        pos++;
+        if (pos < nv - 1) v[pos] = lo[pos] - 1;
+    }
 }
 
 // Exponent reached after `left` steps: first chunk in direction v, then Algorithm 3.

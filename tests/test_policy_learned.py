@@ -82,14 +82,14 @@ def test_trained_policy_gains_over_algorithm_3_with_the_same_result():
     try:
         train = [_instance("quintic_curves", i) for i in range(12, 12 + 48)]
         held = [_instance("quintic_curves", i) for i in range(12)]
-        w, loss, nd = train_policy(ctx, train, hidden=64, epochs=30)
+        w, loss, nd = train_policy(ctx, train, hidden=8, epochs=30)
         assert nd > 1000 and loss < 0.5
         base = sum(z.zeta_plan(s, policy="p_chunk")["game"]["column_steps"] for s in held)
-        learned = sum(z.zeta_plan(s, policy="learned", weights=w, hidden=64)["game"]["column_steps"] for s in held)
-        assert learned < base, (learned, base)
+        learned = sum(z.zeta_plan(s, policy="learned", weights=w, hidden=8)["game"]["column_steps"] for s in held)
+        assert learned < 0.95 * base, (learned, base)   # at least 5% fewer reduction steps than Algorithm 3
         for s in held[:3]:
             P0, _ = z.zeta_charpoly(ctx, s, policy="p_chunk")
-            P1, _ = z.zeta_charpoly(ctx, s, policy="learned", weights=w, hidden=64)
+            P1, _ = z.zeta_charpoly(ctx, s, policy="learned", weights=w, hidden=8)
             assert P0 == P1
     finally:
         z.zeta_destroy(ctx)
