@@ -29,10 +29,11 @@ import zeta_inputs as zi  # noqa: E402
 
 METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
 
-# DRAM traffic of the executor from one ncu capture (profiles/k_execute_quintic_curves_456_full.md):
-# bytes read + written per instance of the quintic workload, valid for this kernel source only.
+# DRAM traffic of the executor from ncu captures of 456 quintics (profiles/k_execute_quintic_curves_456_full.md,
+# profiles/k_execute_quintic_curves_456_learned_full.md): bytes read + written per instance, per policy and path,
+# valid for this kernel source only.
 PROFILED_KERNEL_MD5 = "f80003cbc8a0591ab02e0beb0ed19c5f"
-PROFILED_DRAM_BYTES_PER_INSTANCE = 6.91e9 / 456
+PROFILED_DRAM_BYTES_PER_INSTANCE = {("p_chunk", "vector"): 6.91e9 / 456, ("learned", "vector"): 5.71e9 / 456}
 WORKLOAD = "quintic_curves"
 
 
@@ -288,7 +289,8 @@ def main():
     import hashlib
     src = os.path.join(ROOT, "paper_2602_24155_gb300", "csrc", "zeta_kernels.cu")
     same_kernel = hashlib.md5(open(src, "rb").read()).hexdigest() == PROFILED_KERNEL_MD5
-    traffic = PROFILED_DRAM_BYTES_PER_INSTANCE * args.count if (same_kernel and args.policy == "p_chunk") else None
+    per_inst = PROFILED_DRAM_BYTES_PER_INSTANCE.get((args.policy, getattr(args, "path", "vector")))
+    traffic = per_inst * args.count if (same_kernel and per_inst) else None
     ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
     macs_per_launch = tot["column_steps"] * s * s
     achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12

@@ -64,7 +64,14 @@ typedef enum {
                                     (zeta_options.policy_weights); Algorithm 3 if none is given */
 } zeta_policy;
 
-/* Which kernel runs the recurrence. */
+/* Which kernel runs the recurrence (every path gives the same result).
+ * ZETA_PATH_GEMM: each step M(y) W of Algorithm 2 is an exact fp16 GEMM on
+ * the tensor cores (tcgen05, fp32 accumulation in TMEM): residues become L
+ * balanced base-256 digits (L = ceil((bits(q) + 2) / 8) <= 8), the rows of
+ * M(k-1) and of A are interleaved in one 128-row operand, W's digits form a
+ * Toeplitz operand, and a fused epilogue folds the 2L-1 digit diagonals back
+ * to residues mod q.  It takes instances with s <= 64 and b <= 16 (plane
+ * curves of degree <= 5); others return ZETA_ERR_UNSUPPORTED. */
 typedef enum {
     ZETA_PATH_VECTOR = 0,  /* modular matrix-vector steps on the CUDA cores */
     ZETA_PATH_GEMM = 1     /* exact limb-split modular GEMM steps on the tensor cores */
@@ -202,7 +209,9 @@ zeta_status zeta_batch_release(zeta_batch_plan *plan);
  *  W_t is s x c row-major at W + t*s*c (overwritten); k_t = k[t] >= 0;
  *  q_t = q[t] in [2, 2^63).  Entries must be reduced mod q_t.
  *  All pointers are device pointers; ZETA_ERR_ARG if s or c exceed the
- *  kernel limits (s <= 512, c <= 32). */
+ *  kernel limits (s <= 512, c <= 32; with ZETA_PATH_GEMM s <= 64, c <= 16).
+ *  ZETA_ERR_TIMEOUT if a tensor-core step did not complete within 2 s (the
+ *  kernel stops; the context stays usable). */
 zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
                                const uint32_t *k, const uint64_t *A, const uint64_t *B,
                                uint64_t *W, const uint64_t *q);

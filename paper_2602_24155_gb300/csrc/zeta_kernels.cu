@@ -205,6 +205,10 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
     return cur;
 }
 
+}  // namespace zeta
+#include "zeta_tc.cuh"
+namespace zeta {
+
 // ---------------------------------------------------------------------------
 // Device data of a batch
 // ---------------------------------------------------------------------------
@@ -309,7 +313,7 @@ __host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
 // the section), then store or add the result into the destination block of
 // the next phase, or accumulate x^U g / x^S into H at pole order n.  One
 // block owns an instance, so merges need no atomics.
-template <int CPT, bool MSMEM>
+template <int CPT, bool MSMEM, bool TC>
 __global__ void __launch_bounds__(512) k_execute(
     const DInst *__restrict__ insts, const DTab *__restrict__ tabs, const int32_t *__restrict__ tabpool,
     const uint64_t *__restrict__ secpool, const DChain *__restrict__ chains, const Term *__restrict__ terms,
@@ -317,10 +321,23 @@ __global__ void __launch_bounds__(512) k_execute(
     const uint32_t *__restrict__ order, uint32_t ninst, uint32_t *__restrict__ queue,
     uint64_t *__restrict__ scratch, size_t scratch_stride, uint64_t *__restrict__ blocks, size_t blocks_stride,
     uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint2 s_ct[2 * kTcMaxL];
+    __shared__ uint64_t s_bias;
+    __shared__ int s_abort;
     unsigned long long my_chunks = 0, my_steps = 0;
+    TcState S;
+    if (TC) {
+        tc_setup(&s_tmem, &s_mbar);
+        S.tmem = s_tmem;
+        S.mbar = smem_u32(&s_mbar);
+        S.phase = 0;
+        S.ct = s_ct;
+    }
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         __syncthreads();
@@ -336,8 +353,21 @@ __global__ void __launch_bounds__(512) k_execute(
         const uint64_t *Sec = secpool + I.sec_off;
         const uint32_t *ph = phase_pool + I.phase_off;
         unsigned char *ptr = smem_raw;
-        uint64_t *Ms, *As;
-        if (MSMEM) {
+        uint64_t *Ms = nullptr, *As = nullptr;
+        if (TC) {
+            // operands sized for the largest s of the batch (scratch_stride)
+            const int sKmax = tc_sK((int)scratch_stride);
+            S.Aop = (uint16_t *)ptr;
+            S.Dop = S.Aop + (size_t)128 * kTcMaxL * sKmax;
+            ptr += tc_operand_bytes((int)scratch_stride);
+            S.sK = tc_sK(s);
+            S.L = tc_digits(I.Q.q);
+            tc_constants(I.Q, S.L, s_ct, &s_bias);
+            uint32_t *a32 = reinterpret_cast<uint32_t *>(S.Aop);
+            for (int e = threadIdx.x; e < 128 * S.L * S.sK / 2; e += blockDim.x) a32[e] = 0;
+            __syncthreads();
+            S.bias = s_bias;
+        } else if (MSMEM) {
             Ms = (uint64_t *)ptr;
             As = Ms + (size_t)s * s;
             ptr += (size_t)2 * s * s * sizeof(uint64_t);
@@ -409,29 +439,60 @@ __global__ void __launch_bounds__(512) k_execute(
                     __syncthreads();
                     // A R and M(k-1) R = R_{U-v,v} R from the section (held as Sec R mod q):
                     //   A[r,j] = sum_i v_i Sec[..],  M(k-1)[r,j] = sum_i (U_i - v_i + omega_i) Sec[..]
-                    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-                        const int r = e % s, j = e / s;
-                        const int col = colidx[j];
-                        uint64_t aL = 0, mL = 0, mH = 0;
-                        if (col >= 0) {
-                            for (int i = 0; i < nv; i++) {
-                                const int row = secrow[i * s + r];
-                                if (row < 0) continue;
-                                const uint64_t val = __ldg(&Sec[(size_t)row * I.sec_cols + col]);
-                                aL += val * (uint64_t)sv[i];                       // < d q < 2^63
-                                const uint64_t wm = (uint64_t)(sU[i] - sv[i] + monoS[r * nv + i]);
-                                add128(mL, mH, val * wm);
-                                mH += mul_hi64(val, wm);
-                            }
-                        }
-                        while (aL >= I.Q.q) aL -= I.Q.q;
-                        As[(size_t)j * s + r] = aL;
-                        Ms[(size_t)j * s + r] = reduce128(mL, mH, I.Q);
-                    }
-                    __syncthreads();
                     int res;
-                    if (cur_buf == 0) res = horner_block<CPT>(s, c, k, Ms, As, W, V, I.Q);
-                    else res = horner_block<CPT>(s, c, k, Ms, As, V, W, I.Q);
+                    if (TC) {
+                        // plain residues (one REDC removes R), as digits of the GEMM operand
+                        const int kext = S.L * S.sK;
+                        for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+                            const int r = e % s, j = e / s;
+                            const int col = colidx[j];
+                            uint64_t aL = 0, mL = 0, mH = 0;
+                            if (col >= 0) {
+                                for (int i = 0; i < nv; i++) {
+                                    const int row = secrow[i * s + r];
+                                    if (row < 0) continue;
+                                    const uint64_t val = __ldg(&Sec[(size_t)row * I.sec_cols + col]);
+                                    aL += val * (uint64_t)sv[i];
+                                    const uint64_t wm = (uint64_t)(sU[i] - sv[i] + monoS[r * nv + i]);
+                                    add128(mL, mH, val * wm);
+                                    mH += mul_hi64(val, wm);
+                                }
+                            }
+                            put_digits(S.Aop, 2 * r, j, S.sK, kext, S.L, redc(mL, mH, I.Q));
+                            put_digits(S.Aop, 2 * r + 1, j, S.sK, kext, S.L, redc(aL, 0, I.Q));
+                        }
+                        fence_async_smem();
+                        __syncthreads();
+                        S.cp = tc_cp(c);
+                        S.N = tc_N(S.L, S.cp);
+                        S.drows = tc_drows(S.L, S.cp);
+                        res = cur_buf == 0 ? horner_block_tc(S, s, c, k, W, V, I.Q, &s_abort)
+                                           : horner_block_tc(S, s, c, k, V, W, I.Q, &s_abort);
+                        if (res < 0) goto aborted;
+                    } else {
+                        for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+                            const int r = e % s, j = e / s;
+                            const int col = colidx[j];
+                            uint64_t aL = 0, mL = 0, mH = 0;
+                            if (col >= 0) {
+                                for (int i = 0; i < nv; i++) {
+                                    const int row = secrow[i * s + r];
+                                    if (row < 0) continue;
+                                    const uint64_t val = __ldg(&Sec[(size_t)row * I.sec_cols + col]);
+                                    aL += val * (uint64_t)sv[i];                       // < d q < 2^63
+                                    const uint64_t wm = (uint64_t)(sU[i] - sv[i] + monoS[r * nv + i]);
+                                    add128(mL, mH, val * wm);
+                                    mH += mul_hi64(val, wm);
+                                }
+                            }
+                            while (aL >= I.Q.q) aL -= I.Q.q;
+                            As[(size_t)j * s + r] = aL;
+                            Ms[(size_t)j * s + r] = reduce128(mL, mH, I.Q);
+                        }
+                        __syncthreads();
+                        if (cur_buf == 0) res = horner_block<CPT>(s, c, k, Ms, As, W, V, I.Q);
+                        else res = horner_block<CPT>(s, c, k, Ms, As, V, W, I.Q);
+                    }
                     cur_buf ^= res;
                     if (threadIdx.x == 0) {
                         for (int t = 0; t < nv; t++) sU[t] -= k * sv[t];
@@ -481,6 +542,15 @@ __global__ void __launch_bounds__(512) k_execute(
         for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) out[e] = Hs[e];
         __syncthreads();
     }
+    if (false) {
+    aborted:  // an MMA wait timed out: flag it, wait once more for the MMAs in flight, stop
+        if (threadIdx.x == 0) {
+            atomicAdd(&counters[2], 1ull);
+            mbar_wait(S.mbar, S.phase);
+        }
+        __syncthreads();
+    }
+    if (TC) tc_teardown(S.tmem);
     if (threadIdx.x == 0) {
         atomicAdd(&counters[0], my_chunks);
         atomicAdd(&counters[1], my_steps);
@@ -494,7 +564,7 @@ __global__ void __launch_bounds__(512) k_horner_problems(
     uint32_t count, int s, int c, const uint32_t *__restrict__ kk, const uint64_t *__restrict__ A,
     const uint64_t *__restrict__ B, uint64_t *__restrict__ W, const ModQ *__restrict__ mods,
     uint64_t *__restrict__ scratch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t MASK30 = (1u << 30) - 1;
     unsigned char *ptr = smem_raw;
     uint64_t *Ms, *As;
@@ -535,6 +605,87 @@ __global__ void __launch_bounds__(512) k_horner_problems(
         }
         __syncthreads();
     }
+}
+
+// Kernel-level Algorithm 2 on independent problems with the limb-split GEMM
+// steps on the tensor cores (s <= 64, c <= 16).  status[0] is set if an MMA
+// wait timed out.
+__global__ void __launch_bounds__(kTcThreads) k_horner_problems_tc(
+    uint32_t count, int s, int c, const uint32_t *__restrict__ kk, const uint64_t *__restrict__ A,
+    const uint64_t *__restrict__ B, uint64_t *__restrict__ W, const ModQ *__restrict__ mods,
+    unsigned long long *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint2 s_ct[2 * kTcMaxL];
+    __shared__ uint64_t s_bias;
+    __shared__ int s_abort;
+    const uint32_t MASK30 = (1u << 30) - 1;
+    const int sK = tc_sK(s), cs = pad4(c);
+    uint16_t *Aop = reinterpret_cast<uint16_t *>(smem_raw);
+    uint16_t *Dop = Aop + (size_t)128 * kTcMaxL * sK;
+    uint2 *Wl = reinterpret_cast<uint2 *>(Dop + (size_t)tc_drows(kTcMaxL, 16) * sK);
+    uint2 *Vl = Wl + (size_t)s * cs;
+    tc_setup(&s_tmem, &s_mbar);
+    TcState S;
+    S.Aop = Aop;
+    S.Dop = Dop;
+    S.tmem = s_tmem;
+    S.mbar = smem_u32(&s_mbar);
+    S.phase = 0;
+    S.sK = sK;
+    S.cp = tc_cp(c);
+    S.ct = s_ct;
+    for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const ModQ Q = mods[t];
+        const int k = (int)kk[t];
+        S.L = tc_digits(Q.q);
+        S.N = tc_N(S.L, S.cp);
+        S.drows = tc_drows(S.L, S.cp);
+        tc_constants(Q, S.L, s_ct, &s_bias);
+        const int kext = S.L * sK;
+        uint32_t *a32 = reinterpret_cast<uint32_t *>(Aop);
+        for (int e = threadIdx.x; e < 128 * kext / 2; e += blockDim.x) a32[e] = 0;
+        __syncthreads();
+        S.bias = s_bias;
+        const uint64_t *At_g = A + (size_t)t * s * s;
+        const uint64_t *Bt_g = B + (size_t)t * s * s;
+        uint64_t *Wt = W + (size_t)t * s * c;
+        for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+            const int r = e / s, j = e - r * s;  // row-major input
+            const uint64_t a = At_g[e];
+            const uint64_t x = addmod(mul_small(a, (uint64_t)(k > 0 ? k - 1 : 0), Q), Bt_g[e], Q.q);
+            put_digits(Aop, 2 * r, j, sK, kext, S.L, x);
+            put_digits(Aop, 2 * r + 1, j, sK, kext, S.L, a);
+        }
+        for (int e = threadIdx.x; e < s * cs; e += blockDim.x) {
+            const int j = e / cs, col = e - j * cs;
+            const uint64_t w = col < c ? Wt[j * c + col] : 0;
+            Wl[e] = make_uint2((uint32_t)w & MASK30, (uint32_t)(w >> 30));
+        }
+        fence_async_smem();
+        __syncthreads();
+        const int res = horner_block_tc(S, s, c, k, Wl, Vl, Q, &s_abort);
+        if (res < 0) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, 1ull);
+                mbar_wait(S.mbar, S.phase);  // the MMAs in flight, bounded again
+            }
+            break;
+        }
+        const uint2 *R = res ? Vl : Wl;
+        for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
+            const int j = e / c, col = e - j * c;
+            Wt[e] = ((uint64_t)R[j * cs + col].y << 30) | R[j * cs + col].x;
+        }
+        __syncthreads();
+    }
+    tc_teardown(S.tmem);
+}
+
+// Dynamic shared memory of k_horner_problems_tc.
+inline size_t tc_problem_smem(int s, int c) {
+    return tc_operand_bytes(s) + (size_t)2 * s * pad4(c) * sizeof(uint2);
 }
 
 // ---------------------------------------------------------------------------
@@ -687,9 +838,12 @@ struct DeviceBatch {
     unsigned long long *d_counters = nullptr;
     int grid = 1, threads = 256;
     bool msmem = true;
+    bool tc = false;
     size_t smem = 0, scratch_stride = 0, blocks_stride = 0, h_stride = 0;
     uint64_t bytes = 0, bytes_h2d = 0, bytes_d2h = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // around each recurrence launch
+    cudaGraphExec_t graph_exec = nullptr;                      // captured launches of one run
+    cudaStream_t cap_stream = nullptr;
     double ms_kernel = 0;
     uint64_t launches = 0;
 };
@@ -721,6 +875,8 @@ static zeta_status dev_upload(DeviceEngine *e, DeviceBatch *B, const std::vector
 
 void engine_release(DeviceBatch *B) {
     if (!B) return;
+    if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
+    if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
     for (auto &ev : B->events) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);
@@ -866,20 +1022,44 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     UP(dchunks, d_chunks);
     UP(order, d_order);
 #undef UP
-    B->smem = chain_smem(max_s, max_c, max_h);
-    B->msmem = mats_in_smem(max_s);
-    B->threads = launch_threads(max_s, max_c);
-    const void *kfn = B->msmem ? (const void *)k_execute<4, true> : (const void *)k_execute<4, false>;
+    if (path != ZETA_PATH_VECTOR && path != ZETA_PATH_GEMM) {
+        err = "unknown path";
+        engine_release(B);
+        return ZETA_ERR_ARG;
+    }
+    if (path == ZETA_PATH_GEMM && (max_s > kTcMaxS || max_c > kTcMaxC)) {
+        err = "the tensor-core path takes s <= 64 and b <= 16";
+        engine_release(B);
+        return ZETA_ERR_UNSUPPORTED;
+    }
+    B->tc = path == ZETA_PATH_GEMM;
+    const void *kfn;
+    if (B->tc) {
+        // Ms/As are replaced by the GEMM operands; at most two blocks per SM
+        // (their accumulators fill the 512 TMEM columns)
+        B->smem = tc_operand_bytes(max_s) + chain_smem(max_s, max_c, max_h) - (size_t)2 * max_s * max_s * 8 *
+                                                                                  (mats_in_smem(max_s) ? 1 : 0);
+        B->msmem = false;
+        B->threads = kTcThreads;
+        kfn = (const void *)k_execute<4, false, true>;
+    } else {
+        B->smem = chain_smem(max_s, max_c, max_h);
+        B->msmem = mats_in_smem(max_s);
+        B->threads = launch_threads(max_s, max_c);
+        kfn = B->msmem ? (const void *)k_execute<4, true, false> : (const void *)k_execute<4, false, false>;
+    }
     CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, B->threads, B->smem));
     per_sm = std::max(1, per_sm);
+    if (B->tc) per_sm = std::min(per_sm, 2);
     B->grid = std::max(1, (int)std::min<size_t>((size_t)e->sms * per_sm, batch.size()));
-    B->scratch_stride = (size_t)2 * max_s * max_s;
+    // the tensor-core kernel reads the largest s of the batch from this argument
+    B->scratch_stride = B->tc ? (size_t)max_s : (size_t)2 * max_s * max_s;
     B->blocks_stride = 2 * std::max<size_t>(max_block_words, 1);
     B->h_stride = (size_t)max_h * max_c;
 #define AL(count, ptr) if ((st = dev_alloc(B, count, &B->ptr, err))) { engine_release(B); return st; }
-    AL(B->msmem ? 1 : B->scratch_stride * B->grid, d_scratch);
+    AL((B->msmem || B->tc) ? 1 : B->scratch_stride * B->grid, d_scratch);
     AL(B->blocks_stride * B->grid, d_blocks);
     AL(B->h_stride * batch.size(), d_H);
     AL(16, d_queue);
@@ -889,24 +1069,55 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     return ZETA_OK;
 }
 
+// Enqueue one run of the batch (counter resets and the persistent kernel) on `st`.
+static cudaError_t enqueue_batch(DeviceBatch *B, cudaStream_t st) {
+    cudaError_t ce = cudaMemsetAsync(B->d_queue, 0, 16 * sizeof(uint32_t), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(B->d_counters, 0, 8 * sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) return ce;
+#define LAUNCH(MS, TC)                                                                                      \
+    k_execute<4, MS, TC><<<B->grid, B->threads, B->smem, st>>>(                                             \
+        B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
+        B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
+        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
+    if (B->tc) LAUNCH(false, true);
+    else if (B->msmem) LAUNCH(true, false);
+    else LAUNCH(false, false);
+#undef LAUNCH
+    return cudaGetLastError();
+}
+
+// The first run of a prepared batch captures its launches into a CUDA graph
+// (on a private stream, so that the caller's stream may be the legacy default
+// stream); every run replays the graph on the engine's stream.
 zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaSetDevice(e->device));
-    CUDA_TRY(cudaMemsetAsync(B->d_queue, 0, 16 * sizeof(uint32_t), e->stream));
-    CUDA_TRY(cudaMemsetAsync(B->d_counters, 0, 8 * sizeof(unsigned long long), e->stream));
+    if (!B->graph_exec) {
+        if (!B->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ce = enqueue_batch(B, B->cap_stream);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce2 = cudaStreamEndCapture(B->cap_stream, &g);
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            err = std::string("graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2);
+            cudaGetLastError();
+            return ZETA_ERR_DEVICE;
+        }
+        const cudaError_t ce3 = cudaGraphInstantiate(&B->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce3 != cudaSuccess) {
+            B->graph_exec = nullptr;
+            err = std::string("graph instantiate: ") + cudaGetErrorString(ce3);
+            cudaGetLastError();
+            return ZETA_ERR_DEVICE;
+        }
+    }
     cudaEvent_t ev0, ev1;
     CUDA_TRY(cudaEventCreate(&ev0));
     CUDA_TRY(cudaEventCreate(&ev1));
     B->events.push_back({ev0, ev1});
     CUDA_TRY(cudaEventRecord(ev0, e->stream));
-#define LAUNCH(MS)                                                                                          \
-    k_execute<4, MS><<<B->grid, B->threads, B->smem, e->stream>>>(                                          \
-        B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
-        B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
-        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
-    if (B->msmem) LAUNCH(true);
-    else LAUNCH(false);
-#undef LAUNCH
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaGraphLaunch(B->graph_exec, e->stream));
     CUDA_TRY(cudaEventRecord(ev1, e->stream));
     return ZETA_OK;
 }
@@ -938,6 +1149,10 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
         X->column_steps = X->plan.column_steps;
         X->chunks = X->plan.chunks_played;
         played += X->plan.chunks_played;
+    }
+    if (hc[2]) {
+        err = "a tensor-core step timed out";
+        return ZETA_ERR_TIMEOUT;
     }
     if (hc[0] != played) {  // counters are reset by every launch
         err = "device played a different number of chunks than planned";
@@ -971,9 +1186,13 @@ zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_pol
 zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
                           const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
                           const uint64_t *q, std::string &err) {
-    (void)path;
     CUDA_TRY(cudaSetDevice(e->device));
     if (s == 0 || c == 0 || s > kMaxS || c > kMaxC) { err = "s or c out of range"; return ZETA_ERR_ARG; }
+    if (path == ZETA_PATH_GEMM && (s > (uint32_t)kTcMaxS || c > (uint32_t)kTcMaxC)) {
+        err = "the tensor-core path takes s <= 64 and c <= 16";
+        return ZETA_ERR_ARG;
+    }
+    if (path != ZETA_PATH_VECTOR && path != ZETA_PATH_GEMM) { err = "unknown path"; return ZETA_ERR_ARG; }
     if (count == 0) return ZETA_OK;
     std::vector<uint64_t> hq(count);
     CUDA_TRY(cudaMemcpy(hq.data(), q, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost));
@@ -988,6 +1207,27 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
     ModQ *d_mods;
     zeta_status st = upload(e, "hmods", mods, &d_mods, err);
     if (st) return st;
+    if (path == ZETA_PATH_GEMM) {
+        unsigned long long *d_status;
+        if ((st = ensure(e, "hstatus", sizeof(unsigned long long), (void **)&d_status, err))) return st;
+        const size_t smem = tc_problem_smem((int)s, (int)c);
+        CUDA_TRY(cudaFuncSetAttribute((const void *)k_horner_problems_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        int per_sm = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_horner_problems_tc, kTcThreads,
+                                                               smem));
+        per_sm = std::max(1, std::min(per_sm, 2));  // two blocks' accumulators fill the 512 TMEM columns
+        const int grid = (int)std::min<uint32_t>(count, (uint32_t)(e->sms * per_sm));
+        CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(unsigned long long), e->stream));
+        k_horner_problems_tc<<<grid, kTcThreads, smem, e->stream>>>(count, (int)s, (int)c, k, A, B, W, d_mods,
+                                                                     d_status);
+        CUDA_TRY(cudaGetLastError());
+        unsigned long long flag = 0;
+        CUDA_TRY(cudaMemcpyAsync(&flag, d_status, sizeof(flag), cudaMemcpyDeviceToHost, e->stream));
+        CUDA_TRY(cudaStreamSynchronize(e->stream));
+        if (flag) { err = "tensor-core step timed out"; return ZETA_ERR_TIMEOUT; }
+        return ZETA_OK;
+    }
     int grid = (int)std::min<uint32_t>(count, (uint32_t)e->sms * 4);
     uint64_t *d_scratch;
     if ((st = ensure(e, "hscratch", sizeof(uint64_t) * 2 * s * s * (size_t)grid, (void **)&d_scratch, err))) return st;
@@ -1035,7 +1275,7 @@ __global__ void __launch_bounds__(512) k_horner_problems_static(
     uint32_t count, int s, int c, const uint32_t *__restrict__ kk, const uint64_t *__restrict__ A,
     const uint64_t *__restrict__ B, uint64_t *__restrict__ W, const uint64_t *__restrict__ qv,
     uint64_t *__restrict__ scratch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t MASK30 = (1u << 30) - 1;
     uint64_t *Ms = scratch + (size_t)blockIdx.x * 2 * s * s;
     uint64_t *As = Ms + (size_t)s * s;
