@@ -314,7 +314,7 @@ __host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
 // the next phase, or accumulate x^U g / x^S into H at pole order n.  One
 // block owns an instance, so merges need no atomics.
 template <int CPT, bool MSMEM, bool TC>
-__global__ void __launch_bounds__(512) k_execute(
+__global__ void __launch_bounds__(TC ? kTcThreads : 512) k_execute(
     const DInst *__restrict__ insts, const DTab *__restrict__ tabs, const int32_t *__restrict__ tabpool,
     const uint64_t *__restrict__ secpool, const DChain *__restrict__ chains, const Term *__restrict__ terms,
     const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
@@ -325,18 +325,19 @@ __global__ void __launch_bounds__(512) k_execute(
     __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ uint2 s_ct[2 * kTcMaxL];
-    __shared__ uint64_t s_bias;
-    __shared__ int s_abort;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ uint2 s_ct[2 * kTcMaxL], s_ct_odd[2 * 16];
+    __shared__ int s_abort[2];
     unsigned long long my_chunks = 0, my_steps = 0;
     TcState S;
     if (TC) {
-        tc_setup(&s_tmem, &s_mbar);
+        tc_setup(&s_tmem, s_mbar);
         S.tmem = s_tmem;
-        S.mbar = smem_u32(&s_mbar);
-        S.phase = 0;
+        S.mbar[0] = smem_u32(&s_mbar[0]);
+        S.mbar[1] = smem_u32(&s_mbar[1]);
+        S.phase[0] = S.phase[1] = 0;
         S.ct = s_ct;
+        S.ct_odd = s_ct_odd;
     }
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
@@ -356,17 +357,14 @@ __global__ void __launch_bounds__(512) k_execute(
         uint64_t *Ms = nullptr, *As = nullptr;
         if (TC) {
             // operands sized for the largest s of the batch (scratch_stride)
-            const int sKmax = tc_sK((int)scratch_stride);
-            S.Aop = (uint16_t *)ptr;
-            S.Dop = S.Aop + (size_t)128 * kTcMaxL * sKmax;
+            tc_carve(S, ptr, (int)scratch_stride);
             ptr += tc_operand_bytes((int)scratch_stride);
             S.sK = tc_sK(s);
             S.L = tc_digits(I.Q.q);
-            tc_constants(I.Q, S.L, s_ct, &s_bias);
+            tc_constants(I.Q, S.L, s_ct);
             uint32_t *a32 = reinterpret_cast<uint32_t *>(S.Aop);
             for (int e = threadIdx.x; e < 128 * S.L * S.sK / 2; e += blockDim.x) a32[e] = 0;
             __syncthreads();
-            S.bias = s_bias;
         } else if (MSMEM) {
             Ms = (uint64_t *)ptr;
             As = Ms + (size_t)s * s;
@@ -463,11 +461,8 @@ __global__ void __launch_bounds__(512) k_execute(
                         }
                         fence_async_smem();
                         __syncthreads();
-                        S.cp = tc_cp(c);
-                        S.N = tc_N(S.L, S.cp);
-                        S.drows = tc_drows(S.L, S.cp);
-                        res = cur_buf == 0 ? horner_block_tc(S, s, c, k, W, V, I.Q, &s_abort)
-                                           : horner_block_tc(S, s, c, k, V, W, I.Q, &s_abort);
+                        res = cur_buf == 0 ? horner_block_tc(S, s, c, k, W, V, I.Q, s_abort)
+                                           : horner_block_tc(S, s, c, k, V, W, I.Q, s_abort);
                         if (res < 0) goto aborted;
                     } else {
                         for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
@@ -544,10 +539,8 @@ __global__ void __launch_bounds__(512) k_execute(
     }
     if (false) {
     aborted:  // an MMA wait timed out: flag it, wait once more for the MMAs in flight, stop
-        if (threadIdx.x == 0) {
-            atomicAdd(&counters[2], 1ull);
-            mbar_wait(S.mbar, S.phase);
-        }
+        if (threadIdx.x == 0) atomicAdd(&counters[2], 1ull);
+        if ((threadIdx.x & 127) == 0) mbar_wait(S.mbar[threadIdx.x >> 7], S.phase[threadIdx.x >> 7]);
         __syncthreads();
     }
     if (TC) tc_teardown(S.tmem);
@@ -616,38 +609,33 @@ __global__ void __launch_bounds__(kTcThreads) k_horner_problems_tc(
     unsigned long long *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ uint2 s_ct[2 * kTcMaxL];
-    __shared__ uint64_t s_bias;
-    __shared__ int s_abort;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ uint2 s_ct[2 * kTcMaxL], s_ct_odd[2 * 16];
+    __shared__ int s_abort[2];
     const uint32_t MASK30 = (1u << 30) - 1;
     const int sK = tc_sK(s), cs = pad4(c);
-    uint16_t *Aop = reinterpret_cast<uint16_t *>(smem_raw);
-    uint16_t *Dop = Aop + (size_t)128 * kTcMaxL * sK;
-    uint2 *Wl = reinterpret_cast<uint2 *>(Dop + (size_t)tc_drows(kTcMaxL, 16) * sK);
-    uint2 *Vl = Wl + (size_t)s * cs;
-    tc_setup(&s_tmem, &s_mbar);
     TcState S;
-    S.Aop = Aop;
-    S.Dop = Dop;
+    tc_carve(S, smem_raw, s);
+    uint16_t *Aop = S.Aop;
+    uint2 *Wl = reinterpret_cast<uint2 *>(smem_raw + tc_operand_bytes(s));
+    uint2 *Vl = Wl + (size_t)s * cs;
+    tc_setup(&s_tmem, s_mbar);
+    S.ct_odd = s_ct_odd;
     S.tmem = s_tmem;
-    S.mbar = smem_u32(&s_mbar);
-    S.phase = 0;
+    S.mbar[0] = smem_u32(&s_mbar[0]);
+    S.mbar[1] = smem_u32(&s_mbar[1]);
+    S.phase[0] = S.phase[1] = 0;
     S.sK = sK;
-    S.cp = tc_cp(c);
     S.ct = s_ct;
     for (uint32_t t = blockIdx.x; t < count; t += gridDim.x) {
         const ModQ Q = mods[t];
         const int k = (int)kk[t];
         S.L = tc_digits(Q.q);
-        S.N = tc_N(S.L, S.cp);
-        S.drows = tc_drows(S.L, S.cp);
-        tc_constants(Q, S.L, s_ct, &s_bias);
+        tc_constants(Q, S.L, s_ct);
         const int kext = S.L * sK;
         uint32_t *a32 = reinterpret_cast<uint32_t *>(Aop);
         for (int e = threadIdx.x; e < 128 * kext / 2; e += blockDim.x) a32[e] = 0;
         __syncthreads();
-        S.bias = s_bias;
         const uint64_t *At_g = A + (size_t)t * s * s;
         const uint64_t *Bt_g = B + (size_t)t * s * s;
         uint64_t *Wt = W + (size_t)t * s * c;
@@ -665,12 +653,11 @@ __global__ void __launch_bounds__(kTcThreads) k_horner_problems_tc(
         }
         fence_async_smem();
         __syncthreads();
-        const int res = horner_block_tc(S, s, c, k, Wl, Vl, Q, &s_abort);
+        const int res = horner_block_tc(S, s, c, k, Wl, Vl, Q, s_abort);
         if (res < 0) {
-            if (threadIdx.x == 0) {
-                atomicOr(status, 1ull);
-                mbar_wait(S.mbar, S.phase);  // the MMAs in flight, bounded again
-            }
+            if (threadIdx.x == 0) atomicOr(status, 1ull);
+            // the MMAs in flight, bounded again
+            if ((threadIdx.x & 127) == 0) mbar_wait(S.mbar[threadIdx.x >> 7], S.phase[threadIdx.x >> 7]);
             break;
         }
         const uint2 *R = res ? Vl : Wl;
