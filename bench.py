@@ -182,7 +182,8 @@ def main():
     ap.add_argument("--policy", default="learned",
                     help="learned (trained here on instances disjoint from the batch), p_chunk, depth_first, var_by_var")
     ap.add_argument("--train-count", type=int, default=96)
-    ap.add_argument("--path", default="vector")
+    ap.add_argument("--path", default="auto", choices=["auto", "vector", "gemm"],
+                    help="auto: the autotuner times the launch configurations on a sample of the batch first")
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -214,6 +215,13 @@ def main():
         learned = {"train_s": time.perf_counter() - t0, "decisions": decisions, "loss": train_loss,
                    "hidden": 8, "train_instances": len(train)}
         opt.update(weights=weights, hidden=8)
+
+    tuning = None
+    if args.path == "auto":
+        # before the timed region, like the training: time the candidates on a sample of the batch
+        t0 = time.perf_counter()
+        tuning = z.zeta_autotune(ctx, specs, **opt)
+        tuning["tune_s"] = time.perf_counter() - t0
 
     # device-resident inputs: prepare once, then time the kernels
     plan = z.zeta_batch_prepare(ctx, specs, **opt)
@@ -272,6 +280,28 @@ def main():
         policies["p_chunk"] = {"zeta_per_s": args.count / (ms_plain / 1000.0), "column_steps": tot_plain["column_steps"],
                                "ms_per_step": ms_plain}
 
+    # the other recurrence path on the same batch and policy (limb-split GEMM on the tensor cores against the
+    # modular matrix-vector steps on the CUDA cores)
+    chosen = tuning["best"]["path"] if tuning else args.path
+    paths = {chosen: {"zeta_per_s": value, "ms_per_step": ms_per_step}}
+    other = "gemm" if chosen == "vector" else "vector"
+    plan3 = z.zeta_batch_prepare(ctx, specs, **dict(opt, path=other))
+    plan3.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan3.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    P_other, _, _ = plan3.finish()
+    plan3.release()
+    assert P_other == P_warm, "paths disagree"
+    ms_other = e0.elapsed_time(e1)
+    paths[other] = {"zeta_per_s": args.count / (ms_other / 1000.0), "ms_per_step": ms_other}
+    for v in paths.values():
+        v["modmac_per_s"] = tot["column_steps"] * s * s / (v["ms_per_step"] / 1000.0)
+
     # end to end through the C ABI with host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -289,7 +319,7 @@ def main():
     import hashlib
     src = os.path.join(ROOT, "paper_2602_24155_gb300", "csrc", "zeta_kernels.cu")
     same_kernel = hashlib.md5(open(src, "rb").read()).hexdigest() == PROFILED_KERNEL_MD5
-    per_inst = PROFILED_DRAM_BYTES_PER_INSTANCE.get((args.policy, getattr(args, "path", "vector")))
+    per_inst = PROFILED_DRAM_BYTES_PER_INSTANCE.get((args.policy, chosen))
     traffic = per_inst * args.count if (same_kernel and per_inst) else None
     ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
     macs_per_launch = tot["column_steps"] * s * s
@@ -304,18 +334,23 @@ def main():
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "steps_per_s": column_steps / (ms_per_step / 1000.0),
         "config": {"workload": "quintic_curves_4096", "n": 2, "d": 5, "count_per_gpu": args.count,
-                   "primes": list(zi.PRIMES_QUINTIC_CURVES), "policy": args.policy, "path": args.path,
+                   "primes": list(zi.PRIMES_QUINTIC_CURVES), "policy": args.policy, "path": chosen,
+                   "block_threads": tuning["best"]["block_threads"] if tuning else 0,
                    "l2": "inputs larger than L2 (%.2f GB resident)" % (tot["bytes_h2d"] / 1e9),
                    "column_steps_per_step": column_steps},
         "e2e": {"value": e2e_value, "unit": "zeta/s", "h2d_bytes_per_step": coeff_bytes + tot_e2e["bytes_h2d"],
                 "d2h_bytes_per_step": tot_e2e["bytes_d2h"] + 16 * sum(len(P) for P in P_e2e)},
         "gpu_launches": args.steps,
         "policies": policies,
+        "paths": paths,
+        "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "k_execute", "ms_per_launch": ms_kernel,
-                     "peak_basis": "152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
-                                   % peaks.get("sm_max_mhz", 2070.0)},
+                     "peak_basis": ("152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
+                                    % peaks.get("sm_max_mhz", 2070.0))
+                                   + ("" if chosen == "vector" else "; tensor-core path: its CUDA-core epilogue "
+                                      "(digit fold and reduction) bounds it, the tensor pipe is the minor share")},
         "clocks": clk,
         "host": {"ms_setup": tot_e2e["ms_host_setup"], "ms_finish": tot_e2e["ms_host_finish"],
                  "e2e_s": e2e_s},

@@ -74,7 +74,9 @@ typedef enum {
  * curves of degree <= 5); others return ZETA_ERR_UNSUPPORTED. */
 typedef enum {
     ZETA_PATH_VECTOR = 0,  /* modular matrix-vector steps on the CUDA cores */
-    ZETA_PATH_GEMM = 1     /* exact limb-split modular GEMM steps on the tensor cores */
+    ZETA_PATH_GEMM = 1,    /* exact limb-split modular GEMM steps on the tensor cores */
+    ZETA_PATH_AUTO = 2     /* the choice zeta_autotune recorded in the context for the
+                              batch's (n, d); ZETA_PATH_VECTOR with default blocks if none */
 } zeta_path;
 
 typedef struct {
@@ -97,6 +99,9 @@ typedef struct {
      * (layout of zeta_mlp_train) and its hidden width; NULL = Algorithm 3. */
     const float *policy_weights;
     uint32_t policy_hidden;
+    /* ZETA_PATH_VECTOR: threads per block of the recurrence kernel (a
+     * multiple of 32 in [64, 512]; 0 = the library's choice from s and b). */
+    uint32_t block_threads;
 } zeta_options;
 
 /* Stop after the unnormalised columns Y (no division by p^(v-m+1), no
@@ -201,6 +206,34 @@ zeta_status zeta_batch_run(zeta_ctx *ctx, zeta_batch_plan *plan);
 zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *plan, int64_t *P_out, size_t stride,
                               zeta_stats *per_instance, zeta_stats *total);
 zeta_status zeta_batch_release(zeta_batch_plan *plan);
+
+/* Autotuner of the batch engine (the paper has no counterpart: its kernels
+ * are tuned by hand for one GPU).  Times candidate launch configurations of
+ * the recurrence on a sample of the batch (at most `sample` instances, 0 =
+ * 16 per SM, so that each candidate runs in its steady state rather than in
+ * the tail of a short queue; taken with a constant stride so that the mix of
+ * primes is kept):
+ * ZETA_PATH_VECTOR with the default block and with 128, 256 and 384 threads
+ * per block, and ZETA_PATH_GEMM where the instances allow it (s <= 64,
+ * b <= 16).  Every candidate runs the same plans (opt's policy) once; the
+ * time is that launch's CUDA-event time; every candidate's
+ * P(T) must agree (ZETA_ERR_INTERNAL otherwise).  The fastest is recorded in
+ * the context for the sample's (n, d) and used by ZETA_PATH_AUTO.  All
+ * instances must share n and d (ZETA_ERR_ARG otherwise).  Host memory only
+ * for inputs and `out`; synchronous. */
+#define ZETA_TUNE_MAX 8
+typedef struct {
+    uint32_t n, d;                          /* the class the choice applies to */
+    uint32_t sample;                        /* instances timed */
+    uint32_t candidates;                    /* entries used below */
+    uint32_t cand_path[ZETA_TUNE_MAX];      /* zeta_path of each candidate */
+    uint32_t cand_threads[ZETA_TUNE_MAX];   /* block_threads of each candidate (0 = default) */
+    double cand_ms[ZETA_TUNE_MAX];          /* mean kernel time per launch */
+    uint32_t best;                          /* index of the fastest candidate */
+} zeta_tuning;
+
+zeta_status zeta_autotune(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                          uint32_t sample, zeta_tuning *out);
 
 /* Kernel-level entry point: Algorithm 2 on `count` independent problems
  * held in DEVICE memory (parity tests of the recurrence kernels).

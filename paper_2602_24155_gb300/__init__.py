@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(HERE, "libzeta.so")
 
 POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2, "learned": 3}
 POLICY_FEATURES = 17
-PATH = {"vector": 0, "gemm": 1}
+PATH = {"vector": 0, "gemm": 1, "auto": 2}
+PATH_NAME = {v: k for k, v in PATH.items()}
 
 STATUS = {0: "ZETA_OK", 1: "ZETA_ERR_ARG", 2: "ZETA_ERR_NOT_SMOOTH", 3: "ZETA_ERR_UNSUPPORTED",
           4: "ZETA_ERR_PRECISION", 5: "ZETA_ERR_DEVICE", 6: "ZETA_ERR_TIMEOUT", 7: "ZETA_ERR_OOM",
@@ -29,7 +30,7 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
-           "zeta_policy_dataset"]
+           "zeta_policy_dataset", "zeta_autotune"]
 FLAG_Y_ONLY = 1
 
 
@@ -47,7 +48,18 @@ class Hypersurface(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("path", ctypes.c_int), ("r_override", ctypes.c_uint32),
                 ("N_override", ctypes.c_uint32 * 8), ("flags", ctypes.c_uint32),
-                ("policy_weights", ctypes.POINTER(ctypes.c_float)), ("policy_hidden", ctypes.c_uint32)]
+                ("policy_weights", ctypes.POINTER(ctypes.c_float)), ("policy_hidden", ctypes.c_uint32),
+                ("block_threads", ctypes.c_uint32)]
+
+
+TUNE_MAX = 8
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("d", ctypes.c_uint32), ("sample", ctypes.c_uint32),
+                ("candidates", ctypes.c_uint32), ("cand_path", ctypes.c_uint32 * TUNE_MAX),
+                ("cand_threads", ctypes.c_uint32 * TUNE_MAX), ("cand_ms", ctypes.c_double * TUNE_MAX),
+                ("best", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -123,6 +135,8 @@ def _load():
     lib.zeta_batch_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_size_t,
                                       P(Stats), P(Stats)]
     lib.zeta_batch_release.argtypes = [ctypes.c_void_p]
+    lib.zeta_autotune.argtypes = [ctypes.c_void_p, P(Hypersurface), ctypes.c_size_t, P(Options), ctypes.c_uint32,
+                                  P(Tuning)]
     for name in EXPORTS:
         if name != "zeta_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -143,8 +157,10 @@ class _Lazy:
 LIB = _Lazy()
 
 
-def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0):
+def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0,
+             block_threads=0):
     o = Options()
+    o.block_threads = block_threads
     o.flags = FLAG_Y_ONLY if y_only else 0
     if weights is not None:
         w = np.ascontiguousarray(weights, dtype=np.float32)
@@ -443,3 +459,15 @@ def zeta_policy_dataset(spec, **opt):
     _check(None, LIB.zeta_policy_dataset(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(ng), ctypes.byref(nc),
                                          X.ctypes.data, go.ctypes.data, lab.ctypes.data, cost.ctypes.data))
     return X, go, lab, cost
+
+
+def zeta_autotune(ctx, specs, sample=0, **opt):
+    """Times the candidate launch configurations on a sample of `specs` (all of one (n, d)) and records the
+    fastest in the context for path="auto".  Returns {"best": {...}, "candidates": [...], "sample": m}."""
+    arr = _spec_array(specs)
+    o = _options(**opt)
+    t = Tuning()
+    _check(ctx, LIB.zeta_autotune(ctx, arr, len(specs), ctypes.byref(o), sample, ctypes.byref(t)))
+    cands = [{"path": PATH_NAME[t.cand_path[i]], "block_threads": t.cand_threads[i], "ms": t.cand_ms[i]}
+             for i in range(t.candidates)]
+    return {"n": t.n, "d": t.d, "sample": t.sample, "candidates": cands, "best": cands[t.best]}

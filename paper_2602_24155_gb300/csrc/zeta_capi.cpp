@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <new>
 #include <string>
 #include <thread>
@@ -18,7 +19,25 @@ struct zeta_ctx {
     DeviceEngine *engine = nullptr;
     std::string error;
     unsigned threads = 1;
+    std::map<std::pair<uint32_t, uint32_t>, zeta_tuning> tuned;  // zeta_autotune's choice per (n, d)
 };
+
+// ZETA_PATH_AUTO: the recorded choice for the instances' (n, d) (all equal),
+// else the vector path with the default block.
+static void resolve_path(const zeta_ctx *ctx, const std::vector<Instance *> &batch, zeta_options &o) {
+    if (o.path != ZETA_PATH_AUTO) return;
+    o.path = ZETA_PATH_VECTOR;
+    o.block_threads = 0;
+    if (batch.empty()) return;
+    const uint32_t n = batch[0]->n, d = batch[0]->d;
+    for (const Instance *X : batch)
+        if (X->n != n || X->d != d) return;
+    auto it = ctx->tuned.find({n, d});
+    if (it == ctx->tuned.end()) return;
+    const zeta_tuning &t = it->second;
+    o.path = (zeta_path)t.cand_path[t.best];
+    o.block_threads = t.cand_threads[t.best];
+}
 
 static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -121,7 +140,8 @@ static zeta_status run_one(zeta_ctx *ctx, const zeta_hypersurface *hs, const zet
     if (!st) st = schedule_policy(X, o.policy);
     if (st) { ctx->error = X.error; return st; }
     std::vector<Instance *> batch{&X};
-    st = engine_run(ctx->engine, batch, o.policy, o.path, ctx->error, ms_dev);
+    resolve_path(ctx, batch, o);
+    st = engine_run(ctx->engine, batch, o.policy, o.path, o.block_threads, ctx->error, ms_dev);
     if (st) return st;
     st = (o.flags & ZETA_FLAG_Y_ONLY) ? finish_y_only(X) : finish_instance(X);
     if (st) { ctx->error = X.error; return st; }
@@ -191,7 +211,9 @@ zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_
         else if (ctx->error.empty()) ctx->error = X.error;
     P->ms_setup = now_ms() - t0;
     if (!P->ok.empty()) {
-        zeta_status st = engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, &P->dev, ctx->error);
+        resolve_path(ctx, P->ok, P->opt);
+        zeta_status st =
+            engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, P->opt.block_threads, &P->dev, ctx->error);
         if (st) { delete P; return st; }
     }
     *out = P;
@@ -294,6 +316,67 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
     for (auto *P : plans) zeta_batch_release(P);
     if (!st && total) *total = agg;
     return st;
+}
+
+zeta_status zeta_autotune(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                          uint32_t sample, zeta_tuning *out) {
+    if (!ctx || !hs || !count || !out) return ZETA_ERR_ARG;
+    for (size_t i = 1; i < count; i++)
+        if (hs[i].n != hs[0].n || hs[i].d != hs[0].d) return ZETA_ERR_ARG;
+    // default sample: 16 instances per SM, so that every candidate runs in its steady state (a persistent
+    // block takes several instances) rather than in the tail of a short queue
+    const size_t want = std::min<size_t>(count, sample ? sample : (size_t)16 * engine_sm_count(ctx->engine));
+    std::vector<zeta_hypersurface> pick(want);
+    for (size_t i = 0; i < want; i++) pick[i] = hs[i * count / want];
+    zeta_options base = opt ? *opt : default_options();
+    zeta_tuning T;
+    std::memset(&T, 0, sizeof(T));
+    T.n = hs[0].n;
+    T.d = hs[0].d;
+    T.sample = (uint32_t)want;
+    const uint32_t threads[4] = {0, 128, 256, 384};
+    for (uint32_t th : threads) {
+        T.cand_path[T.candidates] = ZETA_PATH_VECTOR;
+        T.cand_threads[T.candidates++] = th;
+    }
+    T.cand_path[T.candidates] = ZETA_PATH_GEMM;  // dropped below if the instances are too large
+    T.cand_threads[T.candidates++] = 0;
+    std::vector<std::vector<int64_t>> results;
+    size_t stride = 0;
+    uint32_t kept = 0;
+    for (uint32_t ci = 0; ci < T.candidates; ci++) {
+        zeta_options o = base;
+        o.path = (zeta_path)T.cand_path[ci];
+        o.block_threads = T.cand_threads[ci];
+        zeta_batch_plan *P = nullptr;
+        zeta_status st = zeta_batch_prepare(ctx, pick.data(), pick.size(), &o, &P);
+        if (st == ZETA_ERR_UNSUPPORTED && o.path == ZETA_PATH_GEMM) { ctx->error.clear(); continue; }
+        if (st) return st;
+        if (!stride)
+            for (const Instance &X : P->inst) stride = std::max<size_t>(stride, (size_t)X.b + 1);
+        st = zeta_batch_run(ctx, P);
+        std::vector<int64_t> buf(2 * pick.size() * std::max<size_t>(stride, 1), 0);
+        zeta_stats tot;
+        if (!st) st = zeta_batch_finish(ctx, P, buf.data(), std::max<size_t>(stride, 1), nullptr, &tot);
+        zeta_batch_release(P);
+        if (st) return st;
+        T.cand_path[kept] = T.cand_path[ci];
+        T.cand_threads[kept] = T.cand_threads[ci];
+        T.cand_ms[kept] = tot.kernel_launches ? tot.ms_kernel / (double)tot.kernel_launches : 0.0;
+        kept++;
+        results.push_back(std::move(buf));
+    }
+    T.candidates = kept;
+    for (size_t i = 1; i < results.size(); i++)
+        if (results[i] != results[0]) {
+            ctx->error = "autotuner candidates disagree";
+            return ZETA_ERR_INTERNAL;
+        }
+    for (uint32_t ci = 1; ci < kept; ci++)
+        if (T.cand_ms[ci] < T.cand_ms[T.best]) T.best = ci;
+    ctx->tuned[{T.n, T.d}] = T;
+    *out = T;
+    return ZETA_OK;
 }
 
 zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, uint32_t s, uint32_t c,

@@ -130,14 +130,15 @@ zeta_status finish_y_only(Instance &X);  // Y = Fin * H only
 struct DeviceEngine;
 DeviceEngine *engine_create(int device, void *stream, std::string &err);
 void engine_destroy(DeviceEngine *e);
-zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy,
-                       zeta_path path, std::string &err, double *ms_device);
+int engine_sm_count(const DeviceEngine *e);
+zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
+                       uint32_t block_threads, std::string &err, double *ms_device);
 // The same in three phases: upload (inputs become resident in device
 // memory), launch (kernels only, asynchronous on the engine's stream),
 // collect (synchronise and read H back).
 struct DeviceBatch;
 zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
-                           DeviceBatch **out, std::string &err);
+                           uint32_t block_threads, DeviceBatch **out, std::string &err);
 zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err);
 zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err);
 void engine_release(DeviceBatch *B);

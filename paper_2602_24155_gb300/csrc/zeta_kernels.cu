@@ -741,6 +741,8 @@ DeviceEngine *engine_create(int device, void *stream, std::string &err) {
     return e;
 }
 
+int engine_sm_count(const DeviceEngine *e) { return e ? e->sms : 0; }
+
 void engine_destroy(DeviceEngine *e) {
     if (!e) return;
     cudaSetDevice(e->device);
@@ -881,7 +883,7 @@ void engine_batch_timing(const DeviceBatch *B, double *ms_kernel, uint64_t *laun
 }
 
 zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
-                           DeviceBatch **out, std::string &err) {
+                           uint32_t block_threads, DeviceBatch **out, std::string &err) {
     *out = nullptr;
     CUDA_TRY(cudaSetDevice(e->device));
     zeta_status st = upload_binom(e, err);
@@ -1033,6 +1035,14 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         B->smem = chain_smem(max_s, max_c, max_h);
         B->msmem = mats_in_smem(max_s);
         B->threads = launch_threads(max_s, max_c);
+        if (block_threads) {
+            if (block_threads % 32 || block_threads < 64 || block_threads > 512) {
+                err = "block_threads must be a multiple of 32 in [64, 512]";
+                engine_release(B);
+                return ZETA_ERR_ARG;
+            }
+            B->threads = (int)block_threads;
+        }
         kfn = B->msmem ? (const void *)k_execute<4, true, false> : (const void *)k_execute<4, false, false>;
     }
     CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
@@ -1149,14 +1159,14 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
 }
 
 zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
-                       std::string &err, double *ms_device) {
+                       uint32_t block_threads, std::string &err, double *ms_device) {
     cudaEvent_t ev0, ev1;
     CUDA_TRY(cudaSetDevice(e->device));
     CUDA_TRY(cudaEventCreate(&ev0));
     CUDA_TRY(cudaEventCreate(&ev1));
     CUDA_TRY(cudaEventRecord(ev0, e->stream));
     DeviceBatch *B = nullptr;
-    zeta_status st = engine_prepare(e, batch, policy, path, &B, err);
+    zeta_status st = engine_prepare(e, batch, policy, path, block_threads, &B, err);
     if (!st) st = engine_launch(e, B, err);
     if (!st) st = engine_collect(e, B, err);
     cudaEventRecord(ev1, e->stream);
