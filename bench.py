@@ -173,6 +173,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+def _latency(per):
+    """Per-instance device times of the last timed launch (ms): own block time and completion since the launch's
+    first instance started, as p50 / p99 / max."""
+    out = {}
+    for key in ("ms_instance", "ms_complete"):
+        v = sorted(x[key] for x in per)
+        if v:
+            out[key] = {"p50": v[len(v) // 2], "p99": v[min(len(v) - 1, (99 * len(v)) // 100)], "max": v[-1]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -247,7 +258,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    P_timed, _, tot = plan.finish()   # kernel-event timing of the timed launches
+    P_timed, per_timed, tot = plan.finish()   # kernel-event timing of the timed launches
     assert P_timed == P_warm
     plan.release()
     ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -343,6 +354,7 @@ def main():
         "gpu_launches": args.steps,
         "policies": policies,
         "paths": paths,
+        "latency": _latency(per_timed),
         "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": traffic,

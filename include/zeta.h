@@ -128,6 +128,10 @@ typedef struct {
     uint64_t kernel_launches;/* launches of the recurrence kernel covered by ms_kernel */
     uint64_t bytes_h2d;      /* bytes copied host -> device (start terms, sections, tables) */
     uint64_t bytes_d2h;      /* bytes copied device -> host (numerators) */
+    /* Per instance of a batch (last launch): time its block spent on it, and
+     * time from the first instance's start to its completion (%globaltimer). */
+    double ms_instance;
+    double ms_complete;
 } zeta_stats;
 
 typedef struct zeta_ctx zeta_ctx;

@@ -70,7 +70,7 @@ class Stats(ctypes.Structure):
                 ("ms_host_setup", ctypes.c_double), ("ms_device", ctypes.c_double),
                 ("ms_host_finish", ctypes.c_double), ("ms_kernel", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
-                ("bytes_d2h", ctypes.c_uint64)]
+                ("bytes_d2h", ctypes.c_uint64), ("ms_instance", ctypes.c_double), ("ms_complete", ctypes.c_double)]
 
     def as_dict(self):
         out = {}

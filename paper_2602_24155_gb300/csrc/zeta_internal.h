@@ -103,6 +103,7 @@ struct Instance {
     std::string error;
     uint64_t nterms = 0, steps = 0, column_steps = 0, chunks = 0;
     double ms_setup = 0, ms_finish = 0;
+    double ms_instance = 0, ms_complete = 0;  // device: own block time, completion since the launch's first start
 };
 
 // Host-side steps (zeta_host.cpp)

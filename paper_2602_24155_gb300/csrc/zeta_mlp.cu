@@ -115,15 +115,20 @@ __global__ void k_mlp_back_rows(const float *__restrict__ params, int H, const f
     }
 }
 
-// Backward, part 2 (one thread per parameter): sums over the rows [r0, r1),
-// deterministic (no atomics).
+// Backward, part 2: parameter gradients as a two-level sum, deterministic (no
+// atomics).  Block row y takes the rows [r0 + y rchunk, r0 + (y+1) rchunk) of
+// [r0, r1) (one thread per parameter) and writes its partial sums to
+// part[y cnt + p]; k_mlp_sum_parts adds the partials in chunk order.
 __global__ void k_mlp_back_params(int H, const float *__restrict__ X, const float *__restrict__ h1,
                                   const float *__restrict__ h2, const float *__restrict__ d1,
-                                  const float *__restrict__ d2, const float *__restrict__ dscore, size_t r0, size_t r1,
-                                  float *__restrict__ grad) {
+                                  const float *__restrict__ d2, const float *__restrict__ dscore, size_t r0_all,
+                                  size_t r1_all, size_t rchunk, float *__restrict__ part) {
     const int F = kPolicyFeatures;
-    const size_t oW1 = 0, ob1 = (size_t)F * H, oW2 = ob1 + H, ob2 = oW2 + (size_t)H * H, ow3 = ob2 + H, ob3 = ow3 + H;
+    const size_t ob1 = (size_t)F * H, oW2 = ob1 + H, ob2 = oW2 + (size_t)H * H, ow3 = ob2 + H, ob3 = ow3 + H;
     const size_t cnt = ob3 + 1;
+    const size_t r0 = r0_all + (size_t)blockIdx.y * rchunk;
+    const size_t r1 = min(r1_all, r0 + rchunk);
+    float *out = part + (size_t)blockIdx.y * cnt;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt; p += (size_t)gridDim.x * blockDim.x) {
         float acc = 0.f;
         if (p < ob1) {
@@ -144,9 +149,21 @@ __global__ void k_mlp_back_params(int H, const float *__restrict__ X, const floa
         } else {
             for (size_t r = r0; r < r1; r++) acc += dscore[r];
         }
+        out[p] = acc;
+    }
+}
+
+__global__ void k_mlp_sum_parts(const float *__restrict__ part, size_t nchunks, size_t cnt, float *__restrict__ grad) {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt; p += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (size_t c = 0; c < nchunks; c++) acc += part[c * cnt + p];
         grad[p] += acc;
     }
 }
+
+// Row chunks of the parameter gradient: at most kMlpMaxChunks, at least 32 rows each.
+constexpr size_t kMlpMaxChunks = 256;
+inline size_t mlp_rchunk(size_t rows) { return std::max<size_t>(32, (rows + kMlpMaxChunks - 1) / kMlpMaxChunks); }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
                        size_t n, float lr, float b1, float b2, float b1t, float b2t, float eps) {
@@ -197,7 +214,7 @@ size_t fwd_smem(int H) { return sizeof(float) * mlp_view(H).count; }
 static zeta_status mlp_step(int H, const float *d_params, const float *d_X, const uint32_t *d_goff,
                             const uint32_t *d_lab, const std::vector<uint32_t> &goff, size_t g0, size_t g1,
                             float inv_groups, float *d_scores, float *d_h1, float *d_h2, float *d_ds, float *d_d1,
-                            float *d_d2, float *d_grad, float *d_loss, cudaStream_t st) {
+                            float *d_d2, float *d_grad, float *d_loss, float *d_part, cudaStream_t st) {
     const size_t r0 = goff[g0], r1 = goff[g1];
     const size_t rows = r1 - r0;
     if (rows == 0) return ZETA_OK;
@@ -212,7 +229,11 @@ static zeta_status mlp_step(int H, const float *d_params, const float *d_X, cons
     k_mlp_back_rows<<<blocks, T, fwd_smem(H), st>>>(d_params, H, d_h1, d_h2, d_ds, r0, r1, d_d1, d_d2);
     MLP_TRY(cudaGetLastError());
     const size_t cnt = mlp_view(H).count;
-    k_mlp_back_params<<<(int)((cnt + T - 1) / T), T, 0, st>>>(H, d_X, d_h1, d_h2, d_d1, d_d2, d_ds, r0, r1, d_grad);
+    const size_t rchunk = mlp_rchunk(rows), nchunks = (rows + rchunk - 1) / rchunk;
+    k_mlp_back_params<<<dim3((unsigned)((cnt + T - 1) / T), (unsigned)nchunks), T, 0, st>>>(
+        H, d_X, d_h1, d_h2, d_d1, d_d2, d_ds, r0, r1, rchunk, d_part);
+    MLP_TRY(cudaGetLastError());
+    k_mlp_sum_parts<<<(int)((cnt + T - 1) / T), T, 0, st>>>(d_part, nchunks, cnt, d_grad);
     MLP_TRY(cudaGetLastError());
     return ZETA_OK;
 }
@@ -290,6 +311,8 @@ extern "C" zeta_status zeta_mlp_grad(zeta_ctx *ctx, uint32_t hidden, const float
     MLP_TRY(mem.alloc(&dl, 1));
     MLP_TRY(mem.alloc(&dgo, ngroups + 1));
     MLP_TRY(mem.alloc(&dlab, ngroups));
+    float *dpart;
+    MLP_TRY(mem.alloc(&dpart, kMlpMaxChunks * v.count));
     MLP_TRY(cudaMemcpy(dp, params, sizeof(float) * v.count, cudaMemcpyHostToDevice));
     MLP_TRY(cudaMemcpy(dX, X, sizeof(float) * n * kPolicyFeatures, cudaMemcpyHostToDevice));
     MLP_TRY(cudaMemcpy(dgo, goff.data(), sizeof(uint32_t) * goff.size(), cudaMemcpyHostToDevice));
@@ -298,7 +321,7 @@ extern "C" zeta_status zeta_mlp_grad(zeta_ctx *ctx, uint32_t hidden, const float
     MLP_TRY(cudaMemset(dl, 0, sizeof(float)));
     MLP_TRY(cudaMemset(dds, 0, sizeof(float) * n));
     zeta_status st = mlp_step(H, dp, dX, dgo, dlab, goff, 0, ngroups, 1.f / (float)std::max<size_t>(ngroups, 1), dsc,
-                              dh1, dh2, dds, dd1, dd2, dg, dl, 0);
+                              dh1, dh2, dds, dd1, dd2, dg, dl, dpart, 0);
     if (st) return st;
     MLP_TRY(cudaMemcpy(grad, dg, sizeof(float) * v.count, cudaMemcpyDeviceToHost));
     if (loss) MLP_TRY(cudaMemcpy(loss, dl, sizeof(float), cudaMemcpyDeviceToHost));
@@ -334,6 +357,8 @@ extern "C" zeta_status zeta_mlp_train(zeta_ctx *ctx, uint32_t hidden, float *par
     MLP_TRY(mem.alloc(&dl, 1));
     MLP_TRY(mem.alloc(&dgo, ngroups + 1));
     MLP_TRY(mem.alloc(&dlab, ngroups));
+    float *dpart;
+    MLP_TRY(mem.alloc(&dpart, kMlpMaxChunks * v.count));
     MLP_TRY(cudaMemcpy(dp, params, sizeof(float) * v.count, cudaMemcpyHostToDevice));
     MLP_TRY(cudaMemcpy(dX, X, sizeof(float) * n * kPolicyFeatures, cudaMemcpyHostToDevice));
     MLP_TRY(cudaMemcpy(dgo, goff.data(), sizeof(uint32_t) * goff.size(), cudaMemcpyHostToDevice));
@@ -348,7 +373,7 @@ extern "C" zeta_status zeta_mlp_train(zeta_ctx *ctx, uint32_t hidden, float *par
             const size_t g1 = std::min(ngroups, g0 + batch_groups);
             MLP_TRY(cudaMemset(dg, 0, sizeof(float) * v.count));
             zeta_status st = mlp_step(H, dp, dX, dgo, dlab, goff, g0, g1, 1.f / (float)(g1 - g0), dsc, dh1, dh2, dds,
-                                      dd1, dd2, dg, dl, 0);
+                                      dd1, dd2, dg, dl, dpart, 0);
             if (st) return st;
             b1t *= b1;
             b2t *= b2;

@@ -37,3 +37,29 @@ def test_device_entry_points_fail_cleanly_without_a_gpu():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_create(0)
     assert e.value.status == 5  # ZETA_ERR_DEVICE: no CPU fallback
+
+
+def test_vector_executor_stays_within_its_register_budget():
+    """k_execute (CUDA-core path) must use <= 96 registers and no local spills: above that a 160-thread block takes
+    more than a quarter of the register file and the quintic batch loses a resident block per SM (about 40 %)."""
+    import re
+    import shutil
+    import subprocess
+    import tempfile
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = os.path.join(ROOT, "paper_2602_24155_gb300", "csrc", "zeta_kernels.cu")
+    with tempfile.TemporaryDirectory() as tmp:
+        out = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
+                              "-c", src, "-o", os.path.join(tmp, "k.o")], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = out.stderr.splitlines()
+    seen = 0
+    for i, line in enumerate(lines):
+        if "Compiling entry function" in line and "k_executeILi4ELb" in line and "ELb0EE" in line:
+            block = " ".join(lines[i:i + 4])
+            regs = int(re.search(r"Used (\d+) registers", block).group(1))
+            spills = re.search(r"(\d+) bytes spill stores", block)
+            assert regs <= 96, (line, regs)
+            assert spills is None or int(spills.group(1)) == 0
+            seen += 1
+    assert seen == 2

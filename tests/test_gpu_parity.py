@@ -170,3 +170,18 @@ def test_full_quintic_workload_sampled_parity(ctx):
             continue
         ref = ozeta.compute_zeta(n, d, p, c)
         assert out[i] == ref.P
+
+
+def test_mixed_degrees_in_one_launch_with_per_instance_latency(ctx):
+    # plane quartics (s = 28, b = 6) and quintics (s = 45, b = 12) over several primes in one persistent launch
+    specs = [_instance("quartic_curve_f11", i) for i in range(6)] + [_instance("quintic_curves", i) for i in range(26)]
+    out, per, total = z.zeta_batch(ctx, specs, policy="p_chunk")
+    assert total["kernel_launches"] == 1
+    for i in (0, 5, 6, 31):
+        assert out[i] == z.zeta_charpoly(ctx, specs[i], policy="p_chunk")[0]
+    assert out[0] == ozeta.compute_zeta(*specs[0]).P
+    lat = [x["ms_instance"] for x in per]
+    done = [x["ms_complete"] for x in per]
+    assert all(v > 0 for v in lat)
+    assert all(dn >= li - 1e-3 for dn, li in zip(done, lat))
+    assert max(done) <= total["ms_kernel"] + 1.0

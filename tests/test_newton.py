@@ -1,0 +1,76 @@
+"""Newton polygons and the p-rank filter of the Newton-strata search (host logic, against closed forms)."""
+from fractions import Fraction
+
+import zeta_inputs as zi
+from oracle import cohomology, zeta as ozeta
+from paper_2602_24155_gb300.newton import (newton_slopes, polygon_label, random_hypersurfaces, unit_roots_mod_p,
+                                           vp)
+
+
+def test_valuation():
+    assert vp(7 ** 5 * 3, 7) == 5 and vp(-49, 7) == 2 and vp(13, 7) == 0
+
+
+def test_elliptic_curves():
+    # ordinary: 1 - aT + pT^2 with p not dividing a; supersingular: a = 0
+    assert newton_slopes([1, -3, 7], 7) == [0, 1]
+    assert newton_slopes([1, 0, 7], 7) == [Fraction(1, 2)] * 2
+    assert newton_slopes([1, 7, 7], 7) == [Fraction(1, 2)] * 2   # p | a still supersingular (v(a) >= 1/2 line)
+
+
+def test_products_of_polygons():
+    # (1 + pT^2)^3: all slopes 1/2;  (1 - T)(1 - p^2 T): slopes 0 and 2 (weight 2)
+    p = 11
+    P = [1, 0, 3 * p, 0, 3 * p * p, 0, p ** 3]
+    assert newton_slopes(P, p) == [Fraction(1, 2)] * 6
+    assert polygon_label(newton_slopes([1, -(1 + p * p), p * p], p)) == "0^1 2^1"
+    # a genus-2 curve of p-rank 1: (1 - aT + pT^2)(1 + pT^2) with p not dividing a
+    a = 2
+    P2 = [1, -a, 2 * p, -a * p, p * p]
+    assert polygon_label(newton_slopes(P2, p)) == "0^1 1/2^2 1^1"
+    assert unit_roots_mod_p(P2, p) == 1
+
+
+def test_random_hypersurfaces_are_seeded():
+    a = random_hypersurfaces(2, 5, 7, 3, seed=4)
+    assert a == random_hypersurfaces(2, 5, 7, 3, seed=4)
+    assert a != random_hypersurfaces(2, 5, 7, 3, seed=5)
+    assert all(len(x[3]) == 21 and all(0 <= v < 7 for v in x[3]) for x in a)
+
+
+def test_filter_precision_gives_p_mod_p_on_the_oracle():
+    # a non-ordinary plane quintic over F_7: the r = 1 truncation gives P mod p, whose degree is the number of
+    # slope-0 segments of the full Newton polygon
+    n, d, p, c, _ = zi.draw_instance("quintic_curves", 12, cohomology.is_smooth)
+    low = ozeta.compute_zeta(n, d, p, c, r=1)
+    full = ozeta.compute_zeta(n, d, p, c)
+    assert [a % p for a in low.P] == [a % p for a in full.P]
+    slopes = newton_slopes(full.P, p)
+    assert unit_roots_mod_p(low.P, p) == slopes.count(0) == 5
+    assert polygon_label(slopes) == "0^5 1/2^2 1^5"
+
+
+def test_k3_height_rule_on_synthetic_polygons():
+    from paper_2602_24155_gb300.newton import k3_height
+    p = 7
+    # height 1: a_1 a unit; height 2: v(a_1) >= 1, v(a_2) = 1; supersingular: v(a_i) >= i
+    base = [1] + [p ** i for i in range(1, 22)]
+    h1 = list(base); h1[1] = 3
+    h2 = list(base); h2[2] = 5 * p
+    h3 = list(base); h3[3] = 2 * p * p
+    assert k3_height(h1, p) == 1 and k3_height(h2, p) == 2 and k3_height(h3, p) == 3
+    assert k3_height(base, p) is None
+
+
+def test_k3_heights_at_precision_one_on_the_oracle():
+    # Fermat quartic surface: supersingular for p = 3 mod 4; a random K3 whose a_1 vanishes mod p (Hasse-Witt, an
+    # independent computation) has height >= 2
+    from oracle import pins
+    from paper_2602_24155_gb300.newton import k3_height
+    low = ozeta.compute_zeta(3, 4, 7, zi.fermat(3, 4), r=1)
+    assert k3_height(low.P, 7) is None
+    n, d, p, c, _ = zi.draw_instance("quartic_k3", 12, cohomology.is_smooth)
+    assert p == 7 and pins.hasse_witt_charpoly_mod_p(n, d, p, c)[1] % p == 0
+    low = ozeta.compute_zeta(n, d, p, c, r=1)
+    assert low.P[1] % p == 0
+    assert k3_height(low.P, p) >= 2
