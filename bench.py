@@ -173,15 +173,40 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
-def _latency(per):
-    """Per-instance device times of the last timed launch (ms): own block time and completion since the launch's
-    first instance started, as p50 / p99 / max."""
-    out = {}
-    for key in ("ms_instance", "ms_complete"):
-        v = sorted(x[key] for x in per)
-        if v:
-            out[key] = {"p50": v[len(v) // 2], "p99": v[min(len(v) - 1, (99 * len(v)) // 100)], "max": v[-1]}
-    return out
+def _k3_survey(z, ctx, stream, torch):
+    """The 512 quartic K3 surfaces over F_7, F_11, F_13 (every tenth sparse) at relative precision 1 in one persistent
+    launch: a_i mod p^i, which decides every finite height (paper_2602_24155_gb300.newton.k3_height)."""
+    from paper_2602_24155_gb300.newton import k3_height
+
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c))
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    count = zi.WORKLOADS["quartic_k3"]["count"]
+    specs = [zi.draw_instance("quartic_k3", i, accept)[:4] for i in range(count)]
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", r=1)
+    plan.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    P, per, tot = plan.finish()
+    plan.release()
+    ms = e0.elapsed_time(e1)
+    hist = {}
+    for (n, d, p, c), Pi in zip(specs, P):
+        h = "failed" if Pi is None else (k3_height(Pi, p) or "inf")
+        hist[str(h)] = hist.get(str(h), 0) + 1
+    return {"workload": "quartic_k3_%d" % count, "primes": [7, 11, 13], "precision": "r = 1 (a_i mod p^i)",
+            "s": 220, "b": 21, "ms_per_launch": ms, "instances_per_s": count / (ms / 1000.0), "launches": 1,
+            "column_steps": tot["column_steps"], "heights": dict(sorted(hist.items()))}
 
 
 def main():
@@ -191,12 +216,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--policy", default="learned",
-                    help="learned (trained here on instances disjoint from the batch), p_chunk, depth_first, var_by_var")
+                    help="learned (trained here on instances disjoint from the batch; it plays on the cover levels), "
+                         "cover, p_chunk, depth_first, var_by_var")
     ap.add_argument("--train-count", type=int, default=96)
     ap.add_argument("--path", default="auto", choices=["auto", "vector", "gemm"],
                     help="auto: the autotuner times the launch configurations on a sample of the batch first")
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-k3", action="store_true", help="skip the K3 height survey (512 surfaces, precision 1)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -258,7 +285,7 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    P_timed, per_timed, tot = plan.finish()   # kernel-event timing of the timed launches
+    P_timed, _, tot = plan.finish()   # kernel-event timing of the timed launches
     assert P_timed == P_warm
     plan.release()
     ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -275,7 +302,11 @@ def main():
     policies = {args.policy: {"zeta_per_s": value, "column_steps": column_steps, "ms_per_step": ms_per_step}}
     if learned is not None:
         policies["learned"].update(learned)
-        plan2 = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", path=args.path)
+    # the paper's plain policy and the cover search on the same batch and path
+    for other in ("p_chunk", "cover"):
+        if other == args.policy:
+            continue
+        plan2 = z.zeta_batch_prepare(ctx, specs, policy=other, path=args.path)
         plan2.run()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -288,8 +319,8 @@ def main():
         plan2.release()
         assert P_plain == P_warm, "policies disagree"
         ms_plain = e0.elapsed_time(e1)
-        policies["p_chunk"] = {"zeta_per_s": args.count / (ms_plain / 1000.0), "column_steps": tot_plain["column_steps"],
-                               "ms_per_step": ms_plain}
+        policies[other] = {"zeta_per_s": args.count / (ms_plain / 1000.0), "column_steps": tot_plain["column_steps"],
+                           "ms_per_step": ms_plain}
 
     # the other recurrence path on the same batch and policy (limb-split GEMM on the tensor cores against the
     # modular matrix-vector steps on the CUDA cores)
@@ -354,7 +385,6 @@ def main():
         "gpu_launches": args.steps,
         "policies": policies,
         "paths": paths,
-        "latency": _latency(per_timed),
         "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
@@ -367,6 +397,8 @@ def main():
         "host": {"ms_setup": tot_e2e["ms_host_setup"], "ms_finish": tot_e2e["ms_host_finish"],
                  "e2e_s": e2e_s},
     }
+    if rank == 0 and world == 1 and not args.no_k3:
+        line["k3_heights"] = _k3_survey(z, ctx, stream, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample_n = max(1, min(cores, 16))

@@ -60,8 +60,10 @@ typedef enum {
     ZETA_POLICY_PCHUNK = 0,      /* Sec. 4.1: chunks of p on the terms of largest norm, then merge */
     ZETA_POLICY_DEPTH_FIRST = 1, /* Sec. 4.2: greedy v, largest chunk, never merge */
     ZETA_POLICY_VAR_BY_VAR = 2,  /* Sec. 4.3: clear u_n, merge, clear u_{n-1}, ... */
-    ZETA_POLICY_LEARNED = 3      /* p-chunk whose chunk directions are proposed by a trained network
+    ZETA_POLICY_LEARNED = 3,     /* p-chunk whose chunk directions are proposed by a trained network
                                     (zeta_options.policy_weights); Algorithm 3 if none is given */
+    ZETA_POLICY_COVER = 4        /* p-chunk levels whose destinations are searched so that terms merge
+                                    (a search over move 2 of the game of Sec. 3.4; not in the paper) */
 } zeta_policy;
 
 /* Which kernel runs the recurrence (every path gives the same result).
@@ -128,10 +130,6 @@ typedef struct {
     uint64_t kernel_launches;/* launches of the recurrence kernel covered by ms_kernel */
     uint64_t bytes_h2d;      /* bytes copied host -> device (start terms, sections, tables) */
     uint64_t bytes_d2h;      /* bytes copied device -> host (numerators) */
-    /* Per instance of a batch (last launch): time its block spent on it, and
-     * time from the first instance's start to its completion (%globaltimer). */
-    double ms_instance;
-    double ms_complete;
 } zeta_stats;
 
 typedef struct zeta_ctx zeta_ctx;

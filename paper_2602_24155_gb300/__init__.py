@@ -17,7 +17,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libzeta.so")
 
-POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2, "learned": 3}
+POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2, "learned": 3, "cover": 4}
 POLICY_FEATURES = 17
 PATH = {"vector": 0, "gemm": 1, "auto": 2}
 PATH_NAME = {v: k for k, v in PATH.items()}
@@ -70,7 +70,7 @@ class Stats(ctypes.Structure):
                 ("ms_host_setup", ctypes.c_double), ("ms_device", ctypes.c_double),
                 ("ms_host_finish", ctypes.c_double), ("ms_kernel", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
-                ("bytes_d2h", ctypes.c_uint64), ("ms_instance", ctypes.c_double), ("ms_complete", ctypes.c_double)]
+                ("bytes_d2h", ctypes.c_uint64)]
 
     def as_dict(self):
         out = {}

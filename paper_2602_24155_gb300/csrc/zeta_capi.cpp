@@ -77,8 +77,6 @@ static void fill_stats(const Instance &X, zeta_stats *st, double ms_device) {
     st->ms_host_setup = X.ms_setup;
     st->ms_device = ms_device;
     st->ms_host_finish = X.ms_finish;
-    st->ms_instance = X.ms_instance;
-    st->ms_complete = X.ms_complete;
 }
 
 static zeta_options default_options() {

@@ -103,7 +103,6 @@ struct Instance {
     std::string error;
     uint64_t nterms = 0, steps = 0, column_steps = 0, chunks = 0;
     double ms_setup = 0, ms_finish = 0;
-    double ms_instance = 0, ms_complete = 0;  // device: own block time, completion since the launch's first start
 };
 
 // Host-side steps (zeta_host.cpp)
@@ -111,6 +110,7 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
                              bool build_reduction, Instance &X);
 zeta_status finish_instance(Instance &X);
 // Plays the policy on the start chains of X and fills X.plan (zeta_policy.cpp).
+zeta_status validate_plan(Instance &X);
 zeta_status schedule_policy(Instance &X, zeta_policy policy);
 
 size_t policy_param_count(int hidden);

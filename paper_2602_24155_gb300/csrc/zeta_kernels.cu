@@ -324,8 +324,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) k_execute(
     const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
     const uint32_t *__restrict__ order, uint32_t ninst, uint32_t *__restrict__ queue,
     uint64_t *__restrict__ scratch, size_t scratch_stride, uint64_t *__restrict__ blocks, size_t blocks_stride,
-    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters,
-    unsigned long long *__restrict__ times) {
+    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
@@ -351,7 +350,6 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) k_execute(
         __syncthreads();
         if (itx >= ninst) break;
         const uint32_t inst = order[itx];
-        if (threadIdx.x == 0) times[2 * inst] = global_ns();
         const DInst I = insts[inst];
         const DTab T = tabs[I.tab];
         const int s = (int)I.s, b = (int)I.b, nv = (int)I.nv, n = (int)I.n, d = (int)I.d;
@@ -542,7 +540,6 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) k_execute(
         uint64_t *out = Hout + (size_t)inst * h_stride;
         for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) out[e] = Hs[e];
         __syncthreads();
-        if (threadIdx.x == 0) times[2 * inst + 1] = global_ns();
     }
     if (false) {
     aborted:  // an MMA wait timed out: flag it, wait once more for the MMAs in flight, stop
@@ -832,7 +829,6 @@ struct DeviceBatch {
     uint32_t *d_order = nullptr, *d_queue = nullptr;
     uint64_t *d_scratch = nullptr, *d_blocks = nullptr, *d_H = nullptr;
     unsigned long long *d_counters = nullptr;
-    unsigned long long *d_times = nullptr;  // per instance: start and end (%globaltimer, ns)
     int grid = 1, threads = 256;
     bool msmem = true;
     bool tc = false;
@@ -1069,7 +1065,6 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     AL(B->h_stride * batch.size(), d_H);
     AL(16, d_queue);
     AL(8, d_counters);
-    AL(2 * batch.size(), d_times);
 #undef AL
     *out = B;
     return ZETA_OK;
@@ -1084,7 +1079,7 @@ static cudaError_t enqueue_batch(DeviceBatch *B, cudaStream_t st) {
     k_execute<4, MS, TC><<<B->grid, B->threads, B->smem, st>>>(                                             \
         B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
         B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
-        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters, B->d_times)
+        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
     if (B->tc) LAUNCH(false, true);
     else if (B->msmem) LAUNCH(true, false);
     else LAUNCH(false, false);
@@ -1132,10 +1127,7 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaSetDevice(e->device));
     std::vector<uint64_t> hH(B->h_stride * B->insts.size());
     unsigned long long hc[8] = {0};
-    std::vector<unsigned long long> ht(2 * B->insts.size());
     CUDA_TRY(cudaMemcpyAsync(hH.data(), B->d_H, sizeof(uint64_t) * hH.size(), cudaMemcpyDeviceToHost, e->stream));
-    CUDA_TRY(cudaMemcpyAsync(ht.data(), B->d_times, sizeof(unsigned long long) * ht.size(), cudaMemcpyDeviceToHost,
-                             e->stream));
     CUDA_TRY(cudaMemcpyAsync(hc, B->d_counters, sizeof(hc), cudaMemcpyDeviceToHost, e->stream));
     CUDA_TRY(cudaStreamSynchronize(e->stream));
     B->bytes_d2h = sizeof(uint64_t) * hH.size();
@@ -1151,12 +1143,8 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     }
     B->events.clear();
     uint64_t played = 0;
-    unsigned long long t_first = ~0ull;
-    for (size_t ii = 0; ii < B->insts.size(); ii++) t_first = std::min(t_first, ht[2 * ii]);
     for (size_t ii = 0; ii < B->insts.size(); ii++) {
         Instance *X = B->insts[ii];
-        X->ms_instance = (double)(ht[2 * ii + 1] - ht[2 * ii]) * 1e-6;
-        X->ms_complete = (double)(ht[2 * ii + 1] - t_first) * 1e-6;
         X->H.assign(hH.begin() + ii * B->h_stride, hH.begin() + ii * B->h_stride + (size_t)X->h_rows * X->b);
         X->steps = X->plan.steps;
         X->column_steps = X->plan.column_steps;

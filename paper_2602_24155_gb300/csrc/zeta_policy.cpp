@@ -13,7 +13,22 @@
 //               directions, so that all terms stay on the pole orders p t.
 //  var-by-var   (Sec. 4.3): phase t = n..0 reduces every term with greedy
 //               chunks until u_t = 0 (or pole order n), then combines.
+//  cover        (this library, a search over move 2 of the game): the levels
+//               of p-chunk, but every term of a level chooses its destination
+//               so that terms land together.  With S = {0..n} every step
+//               lowers each nonzero coordinate by at least 1, so after L
+//               steps a term with all U_i >= L can reach exactly the V with
+//               0 <= V <= U - L 1 and |V| = |U| - d L; a group of terms can
+//               share a destination iff the positive part of the
+//               componentwise minimum of their boxes U - L 1 still sums to
+//               |V|.  Terms first join the next level's start terms they
+//               dominate, then groups grow greedily on the compatibility graph
+//               (seeds in decreasing degree, members keeping the most mass of
+//               the common box); the destination is the point of the common
+//               box proportional to it.  Terms with a coordinate below L, and
+//               the last level (pole order n, no merging), play Algorithm 3.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <functional>
 #include <unordered_map>
@@ -83,10 +98,191 @@ void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_step
     }
 }
 
+// Chunks of a path of L steps from U to V = U - L 1 - E (E >= 0, |E| = (d - nv) L,
+// every U_i >= L): step j lowers every coordinate by 1 and takes d - nv extra
+// units from the list of E's units sorted by coordinate; equal consecutive
+// steps form one chunk.  Every step is legal: all coordinates stay >= 1 until
+// the last step (S = {0..n} is covered) and the pole order stays >= n.
+void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live) {
+    const int nv = (int)X.nv, x = (int)X.d - nv;
+    int rem[kMaxVars];
+    int cur = 0;
+    for (int t = 0; t < nv; t++) rem[t] = U[t] - L - V[t];
+    int prev[kMaxVars];
+    int run = 0;
+    auto flush = [&]() {
+        if (!run) return;
+        PlanChunk c;
+        std::memset(&c, 0, sizeof(c));
+        for (int t = 0; t < nv; t++) c.v[t] = (int8_t)prev[t];
+        c.k = run;
+        X.plan.chunks.push_back(c);
+        for (int t = 0; t < nv; t++) U[t] -= run * prev[t];
+        X.plan.chunks_played++;
+        X.plan.steps += run;
+        X.plan.column_steps += (uint64_t)run * __builtin_popcount(live);
+        X.plan.work += (uint64_t)run * __builtin_popcount(live) * X.s * X.s;
+        run = 0;
+    };
+    for (int j = 0; j < L; j++) {
+        int v[kMaxVars];
+        for (int t = 0; t < nv; t++) v[t] = 1;
+        for (int u = 0; u < x; u++) {
+            while (cur < nv && rem[cur] == 0) cur++;
+            v[cur]++;
+            rem[cur]--;
+        }
+        bool same = run > 0;
+        for (int t = 0; t < nv && same; t++) same = v[t] == prev[t];
+        if (!same) {
+            flush();
+            std::memcpy(prev, v, sizeof(v));
+        }
+        run++;
+    }
+    flush();
+}
+
 uint32_t chain_live(const Instance &X, const Chain &ch) {
     uint32_t m = 0;
     for (uint32_t t = ch.term_begin; t < ch.term_end; t++) m |= 1u << X.terms[t].col;
     return m;
+}
+
+// Destinations of the entries [e0, e1) of a cover level (L steps each): see
+// the policy's description above.  Returns, per entry, its destination V or
+// an empty vector (Algorithm 3).
+std::vector<std::vector<int32_t>> cover_destinations(const Instance &X, const Plan &P, size_t e0, size_t e1,
+                                                     const std::vector<int> &next_starts, int L) {
+    const int nv = (int)X.nv, d = (int)X.d;
+    const size_t E = e1 - e0;
+    std::vector<std::vector<int32_t>> out(E);
+    if (E == 0) return out;
+    const int target = norm(P.entries[e0].U, nv) - d * L;
+    std::vector<int> freeidx;
+    std::vector<std::array<int32_t, kMaxVars>> box(E);
+    for (size_t i = 0; i < E; i++) {
+        const PlanEntry &e = P.entries[e0 + i];
+        bool ok = norm(e.U, nv) - d * L == target;
+        for (int t = 0; t < nv; t++) {
+            box[i][t] = e.U[t] - L;
+            if (box[i][t] < 0) ok = false;
+        }
+        if (ok) freeidx.push_back((int)i);
+    }
+    auto mass = [&](const int32_t *m) {
+        int s = 0;
+        for (int t = 0; t < nv; t++) {
+            if (m[t] < 0) return -1;
+            s += m[t];
+        }
+        return s;
+    };
+    // 1. join a term already bound for the next level that the box dominates (most shared columns): the
+    //    next level's start terms and the destinations of this level's Algorithm-3 terms
+    std::vector<std::array<int32_t, kMaxVars>> fixedV;
+    std::vector<uint32_t> fixedLive;
+    for (int c : next_starts) {
+        std::array<int32_t, kMaxVars> V{};
+        for (int t = 0; t < nv; t++) V[t] = X.chains[c].U[t];
+        fixedV.push_back(V);
+        fixedLive.push_back(chain_live(X, X.chains[c]));
+    }
+    {
+        std::vector<char> is_free(E, 0);
+        for (int i : freeidx) is_free[i] = 1;
+        for (size_t i = 0; i < E; i++) {
+            if (is_free[i]) continue;
+            std::array<int32_t, kMaxVars> u{};
+            for (int t = 0; t < nv; t++) u[t] = P.entries[e0 + i].U[t];
+            int leftsteps = L;
+            while (leftsteps > 0 && norm(u.data(), nv) > (int)X.n) {
+                int v[kMaxVars];
+                greedy_v(u.data(), nv, d, v);
+                const int k = std::min(k_max(u.data(), v, nv, (int)X.n, d), leftsteps);
+                if (k <= 0) break;
+                for (int t = 0; t < nv; t++) u[t] -= k * v[t];
+                leftsteps -= k;
+            }
+            if (norm(u.data(), nv) == target) {
+                fixedV.push_back(u);
+                fixedLive.push_back(P.entries[e0 + i].live);
+            }
+        }
+    }
+    std::vector<int> left;
+    for (int i : freeidx) {
+        const PlanEntry &e = P.entries[e0 + i];
+        int best = -1, best_overlap = -1;
+        for (size_t f = 0; f < fixedV.size(); f++) {
+            bool dom = true;
+            for (int t = 0; t < nv && dom; t++) dom = fixedV[f][t] <= box[i][t];
+            if (!dom) continue;
+            const int ov = __builtin_popcount(fixedLive[f] & e.live);
+            if (ov > best_overlap) { best_overlap = ov; best = (int)f; }
+        }
+        if (best >= 0) out[i].assign(fixedV[best].begin(), fixedV[best].end());
+        else left.push_back(i);
+    }
+    // 2. compatibility graph on the rest, greedy group growth
+    const size_t R = left.size();
+    std::vector<std::vector<int>> comp(R);
+    for (size_t a = 0; a < R; a++)
+        for (size_t b = a + 1; b < R; b++) {
+            int32_t m[kMaxVars];
+            for (int t = 0; t < nv; t++) m[t] = std::min(box[left[a]][t], box[left[b]][t]);
+            if (mass(m) >= target) {
+                comp[a].push_back((int)b);
+                comp[b].push_back((int)a);
+            }
+        }
+    std::vector<int> order(R);
+    for (size_t a = 0; a < R; a++) order[a] = (int)a;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return comp[a].size() > comp[b].size(); });
+    std::vector<char> taken(R, 0);
+    for (int a : order) {
+        if (taken[a]) continue;
+        taken[a] = 1;
+        std::vector<int> grp{a};
+        int32_t m[kMaxVars] = {0};
+        for (int t = 0; t < nv; t++) m[t] = box[left[a]][t];
+        std::vector<int> cand;
+        for (int b : comp[a])
+            if (!taken[b]) cand.push_back(b);
+        while (!cand.empty()) {
+            int best = -1, best_mass = -1;
+            for (int b : cand) {
+                int32_t mm[kMaxVars];
+                for (int t = 0; t < nv; t++) mm[t] = std::min(m[t], box[left[b]][t]);
+                const int ms = mass(mm);
+                if (ms > best_mass) { best_mass = ms; best = b; }
+            }
+            if (best_mass < target) break;
+            for (int t = 0; t < nv; t++) m[t] = std::min(m[t], box[left[best]][t]);
+            taken[best] = 1;
+            grp.push_back(best);
+            std::vector<int> keep;
+            for (int b : cand) {
+                if (taken[b]) continue;
+                int32_t mm[kMaxVars];
+                for (int t = 0; t < nv; t++) mm[t] = std::min(m[t], box[left[b]][t]);
+                if (mass(mm) >= target) keep.push_back(b);
+            }
+            cand.swap(keep);
+        }
+        // destination: the point of the common box m with |V| = target proportional to m
+        const int tot = mass(m);
+        std::vector<int32_t> V(kMaxVars, 0);
+        int sum = 0;
+        for (int t = 0; t < nv; t++) {
+            V[t] = (int32_t)((int64_t)m[t] * target / tot);
+            sum += V[t];
+        }
+        for (int t = 0; sum < target; t = (t + 1) % nv)
+            if (V[t] < m[t]) { V[t]++; sum++; }
+        for (int b : grp) out[left[b]] = V;
+    }
+    return out;
 }
 
 }  // namespace
@@ -130,7 +326,8 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     std::unordered_map<uint64_t, Arr> cur, nxt;
     std::vector<std::vector<int32_t>> curU, nxtU;  // exponents of arrival blocks by index
     auto phase = [&](const std::vector<int> &starts, auto stop_for, auto max_steps,
-                     const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
+                     const std::function<bool(const int32_t *, int, int *)> &choose = nullptr,
+                     const std::vector<int> *cover_next = nullptr, int cover_L = 0) {
         // entries: arrivals of this phase, then start chains (merged into an arrival if equal u)
         P.phase_begin.push_back((uint32_t)P.entries.size());
         std::unordered_map<uint64_t, size_t> entry_of;
@@ -162,12 +359,15 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
         nxt.clear();
         nxtU.clear();
         const size_t e0 = P.phase_begin.back(), e1 = P.entries.size();
+        std::vector<std::vector<int32_t>> dest_of;  // cover: chosen destination per entry (empty = Algorithm 3)
+        if (cover_next) dest_of = cover_destinations(X, P, e0, e1, *cover_next, cover_L);
         for (size_t ei = e0; ei < e1; ei++) {
             PlanEntry &e = P.entries[ei];
             int32_t U[kMaxVars];
             std::memcpy(U, e.U, sizeof(U));
             e.chunk_begin = (uint32_t)P.chunks.size();
-            play_chunks(X, U, e.live, stop_for, max_steps(e), choose);
+            if (cover_next && !dest_of[ei - e0].empty()) path_chunks(X, U, dest_of[ei - e0].data(), cover_L, e.live);
+            else play_chunks(X, U, e.live, stop_for, max_steps(e), choose);
             e.chunk_end = (uint32_t)P.chunks.size();
             if (norm(U, nv) == n) {
                 e.dest = -1;
@@ -198,7 +398,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
         if (st) return st;
         X.plan = Plan();
     }
-    if (policy == ZETA_POLICY_PCHUNK || policy == ZETA_POLICY_LEARNED) {
+    if (policy == ZETA_POLICY_PCHUNK || policy == ZETA_POLICY_LEARNED || policy == ZETA_POLICY_COVER) {
         int tmax = 0;
         std::vector<std::vector<int>> by_level;
         for (size_t c = 0; c < X.chains.size(); c++) {
@@ -218,8 +418,14 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
                 };
             else if (X.teacher)
                 choose = [&X](const int32_t *U, int left, int *v) { return teacher_direction(X, U, left, v); };
-            phase(t < (int)by_level.size() ? by_level[t] : std::vector<int>(),
-                  [](const int32_t *) { return false; }, [&](const PlanEntry &) { return steps; }, choose);
+            // the learned policy plays on the cover levels: searched destinations where a term's box allows,
+            // the network's directions for the others
+            const bool cover = (policy == ZETA_POLICY_COVER || (policy == ZETA_POLICY_LEARNED && X.net.w)) &&
+                               t >= 2 && d >= nv;
+            const std::vector<int> none;
+            phase(t < (int)by_level.size() ? by_level[t] : none, [](const int32_t *) { return false; },
+                  [&](const PlanEntry &) { return steps; }, choose,
+                  cover ? (t - 1 < (int)by_level.size() ? &by_level[t - 1] : &none) : nullptr, steps);
         }
     } else if (policy == ZETA_POLICY_VAR_BY_VAR) {
         std::vector<int> all(X.chains.size());
@@ -234,6 +440,66 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
         return X.status = ZETA_ERR_ARG;
     }
     P.phase_begin.push_back((uint32_t)P.entries.size());
+    return validate_plan(X);
+}
+
+// Every chunk of the plan is a legal move of the game (Prop. 3.3 with
+// S = {0..n}: |v| = d, v <= u, u_i != 0 => v_i != 0, k >= 1, pole order >= n
+// after the chunk) and every entry ends where its routing says: at the
+// exponent of its destination block, or at pole order n.
+zeta_status validate_plan(Instance &X) {
+    const Plan &P = X.plan;
+    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
+    for (size_t ph = 0; ph + 1 < P.phase_begin.size(); ph++) {
+        std::unordered_map<int32_t, std::vector<int32_t>> dest_U;
+        for (uint32_t ei = P.phase_begin[ph]; ei < P.phase_begin[ph + 1]; ei++) {
+            const PlanEntry &e = P.entries[ei];
+            int32_t U[kMaxVars];
+            std::memcpy(U, e.U, sizeof(U));
+            for (uint32_t ci = e.chunk_begin; ci < e.chunk_end; ci++) {
+                const PlanChunk &c = P.chunks[ci];
+                int sv = 0;
+                bool ok = c.k >= 1;
+                for (int t = 0; t < nv; t++) {
+                    sv += c.v[t];
+                    if (c.v[t] < 0 || U[t] - c.k * c.v[t] < 0 || (U[t] != 0 && c.v[t] == 0)) ok = false;
+                }
+                if (!ok || sv != d) {
+                    X.error = "plan has an illegal chunk";
+                    return X.status = ZETA_ERR_INTERNAL;
+                }
+                for (int t = 0; t < nv; t++) U[t] -= c.k * c.v[t];
+                if (norm(U, nv) < n) {
+                    X.error = "plan goes below pole order n";
+                    return X.status = ZETA_ERR_INTERNAL;
+                }
+            }
+            if (e.dest < 0) {
+                if (norm(U, nv) != n) {
+                    X.error = "plan leaves a term above pole order n";
+                    return X.status = ZETA_ERR_INTERNAL;
+                }
+                continue;
+            }
+            auto it = dest_U.find(e.dest);
+            if (it == dest_U.end()) dest_U.emplace(e.dest, std::vector<int32_t>(U, U + nv));
+            else if (!std::equal(U, U + nv, it->second.begin())) {
+                X.error = "plan merges different exponents";
+                return X.status = ZETA_ERR_INTERNAL;
+            }
+        }
+        // the next phase's arrivals start where their block's entries ended
+        if (ph + 2 < P.phase_begin.size())
+            for (uint32_t ei = P.phase_begin[ph + 1]; ei < P.phase_begin[ph + 2]; ei++) {
+                const PlanEntry &e = P.entries[ei];
+                if (e.arrival < 0) continue;
+                auto it = dest_U.find(e.arrival);
+                if (it == dest_U.end() || !std::equal(e.U, e.U + nv, it->second.begin())) {
+                    X.error = "plan arrival does not match its block";
+                    return X.status = ZETA_ERR_INTERNAL;
+                }
+            }
+    }
     return ZETA_OK;
 }
 

@@ -43,3 +43,23 @@ def test_method_1_search_finds_non_ordinary_curves(ctx):
             slopes = newton_slopes(P, 7)
             assert slopes.count(0) <= 5 and len(slopes) == 12
             assert slopes == sorted(1 - x for x in slopes)   # symmetric (functional equation)
+
+
+def test_k3_heights_from_a_precision_one_batch(ctx):
+    """Quartic K3 surfaces (s = 220, b = 21) in one launch at relative precision 1: heights checked against the
+    Hasse-Witt matrix (a_1 mod p, an independent computation), the Fermat surfaces (supersingular for p = 3 mod 4)
+    and the oracle's own precision-1 run."""
+    import zeta_inputs as zi
+    from oracle import cohomology, pins, zeta as ozeta
+    from paper_2602_24155_gb300.newton import k3_heights
+    idx = list(range(8)) + [12, 24]
+    specs = [zi.draw_instance("quartic_k3", i, cohomology.is_smooth)[:4] for i in idx]
+    specs += [(3, 4, 7, zi.fermat(3, 4)), (3, 4, 13, zi.fermat(3, 4))]
+    heights, per, tot = k3_heights(ctx, specs)
+    assert tot["kernel_launches"] == 1 and all(h is not None for h in heights)
+    assert heights[-2] == "inf" and heights[-1] == 1
+    for (n, d, p, c), h in zip(specs[:-2], heights[:-2]):
+        a1 = pins.hasse_witt_charpoly_mod_p(n, d, p, c)[1] % p
+        assert (h == 1) == (a1 != 0)
+    P_gpu = z.zeta_charpoly(ctx, specs[8], policy="p_chunk", r=1)[0]
+    assert P_gpu == ozeta.compute_zeta(*specs[8], r=1).P

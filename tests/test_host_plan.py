@@ -124,3 +124,22 @@ def test_host_game_matches_the_oracle_game(policy, which):
     g = plan["game"]
     assert (g["chunks"], g["steps"], g["merges"]) == (res.log.chunks, res.log.steps, res.log.merges)
     assert g["column_steps"] >= res.log.column_steps
+
+
+def test_cover_policy_plays_fewer_column_steps_with_valid_plans():
+    """The cover search (destinations chosen so that terms merge) against p-chunk on the same instances; every
+    plan passes the library's legality check (zeta_plan fails otherwise)."""
+    import zeta_inputs as zi
+    import paper_2602_24155_gb300 as z
+    from oracle import cohomology
+    tot = {"p_chunk": 0, "cover": 0}
+    for i in range(6):
+        n, d, p, c, _ = zi.draw_instance("quintic_curves", i, cohomology.is_smooth)
+        for pol in tot:
+            tot[pol] += z.zeta_plan((n, d, p, c), policy=pol)["game"]["column_steps"]
+    assert tot["cover"] < 0.85 * tot["p_chunk"]
+    # K3: d = n + 1 leaves no freedom in the destinations, the cover game is the p-chunk game
+    n, d, p, c, _ = zi.draw_instance("quartic_k3", 3, cohomology.is_smooth)
+    a = z.zeta_plan((n, d, p, c), policy="cover", r=1)["game"]
+    b = z.zeta_plan((n, d, p, c), policy="p_chunk", r=1)["game"]
+    assert a["column_steps"] == b["column_steps"]
