@@ -152,8 +152,9 @@ uint32_t chain_live(const Instance &X, const Chain &ch) {
 // Destinations of the entries [e0, e1) of a cover level (L steps each): see
 // the policy's description above.  Returns, per entry, its destination V or
 // an empty vector (Algorithm 3).
-std::vector<std::vector<int32_t>> cover_destinations(const Instance &X, const Plan &P, size_t e0, size_t e1,
-                                                     const std::vector<int> &next_starts, int L) {
+std::vector<std::vector<int32_t>> cover_destinations(
+    const Instance &X, const Plan &P, size_t e0, size_t e1, const std::vector<int> &next_starts, int L,
+    const std::function<bool(const int32_t *, int, int *)> &choose) {
     const int nv = (int)X.nv, d = (int)X.d;
     const size_t E = e1 - e0;
     std::vector<std::vector<int32_t>> out(E);
@@ -179,7 +180,8 @@ std::vector<std::vector<int32_t>> cover_destinations(const Instance &X, const Pl
         return s;
     };
     // 1. join a term already bound for the next level that the box dominates (most shared columns): the
-    //    next level's start terms and the destinations of this level's Algorithm-3 terms
+    //    next level's start terms and the destinations of this level's other terms (Algorithm 3, or the
+    //    network's directions under the learned policy)
     std::vector<std::array<int32_t, kMaxVars>> fixedV;
     std::vector<uint32_t> fixedLive;
     for (int c : next_starts) {
@@ -197,8 +199,8 @@ std::vector<std::vector<int32_t>> cover_destinations(const Instance &X, const Pl
             for (int t = 0; t < nv; t++) u[t] = P.entries[e0 + i].U[t];
             int leftsteps = L;
             while (leftsteps > 0 && norm(u.data(), nv) > (int)X.n) {
-                int v[kMaxVars];
-                greedy_v(u.data(), nv, d, v);
+                int v[kMaxVars];  // the direction the level will play (the same chooser as play_chunks)
+                if (!(choose && choose(u.data(), leftsteps, v))) greedy_v(u.data(), nv, d, v);
                 const int k = std::min(k_max(u.data(), v, nv, (int)X.n, d), leftsteps);
                 if (k <= 0) break;
                 for (int t = 0; t < nv; t++) u[t] -= k * v[t];
@@ -360,7 +362,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
         nxtU.clear();
         const size_t e0 = P.phase_begin.back(), e1 = P.entries.size();
         std::vector<std::vector<int32_t>> dest_of;  // cover: chosen destination per entry (empty = Algorithm 3)
-        if (cover_next) dest_of = cover_destinations(X, P, e0, e1, *cover_next, cover_L);
+        if (cover_next) dest_of = cover_destinations(X, P, e0, e1, *cover_next, cover_L, choose);
         for (size_t ei = e0; ei < e1; ei++) {
             PlanEntry &e = P.entries[ei];
             int32_t U[kMaxVars];
