@@ -251,6 +251,15 @@ zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, ui
                                const uint32_t *k, const uint64_t *A, const uint64_t *B,
                                uint64_t *W, const uint64_t *q);
 
+/* Self-test of the bounded waits (the paper has no counterpart): one block on
+ * the CURRENT device waits on a barrier that nothing arrives on, with the same
+ * kind of deadline the tensor-core kernels use for their MMA waits, and gives
+ * up after limit_ms (1..10000).  Returns ZETA_ERR_TIMEOUT when the wait ran out
+ * (the expected outcome) and the time waited in *waited_ms (may be NULL); the
+ * context stays usable.  No tensor core, TMEM or global memory beyond an
+ * 16-byte status word is touched. */
+zeta_status zeta_selftest_wait(zeta_ctx *ctx, uint32_t limit_ms, double *waited_ms);
+
 /* Allocation-free form of zeta_horner_device, for callers that cannot
  * allocate device memory: code running inside another framework's memory
  * pool or a fixed memory budget, plugins that must not call cudaMalloc (or

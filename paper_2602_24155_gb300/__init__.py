@@ -30,7 +30,7 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
-           "zeta_policy_dataset", "zeta_autotune"]
+           "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait"]
 FLAG_Y_ONLY = 1
 
 
@@ -135,6 +135,7 @@ def _load():
     lib.zeta_batch_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_size_t,
                                       P(Stats), P(Stats)]
     lib.zeta_batch_release.argtypes = [ctypes.c_void_p]
+    lib.zeta_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
     lib.zeta_autotune.argtypes = [ctypes.c_void_p, P(Hypersurface), ctypes.c_size_t, P(Options), ctypes.c_uint32,
                                   P(Tuning)]
     for name in EXPORTS:
@@ -471,3 +472,10 @@ def zeta_autotune(ctx, specs, sample=0, **opt):
     cands = [{"path": PATH_NAME[t.cand_path[i]], "block_threads": t.cand_threads[i], "ms": t.cand_ms[i]}
              for i in range(t.candidates)]
     return {"n": t.n, "d": t.d, "sample": t.sample, "candidates": cands, "best": cands[t.best]}
+
+
+def zeta_selftest_wait(ctx, limit_ms):
+    """Runs the bounded-wait self-test; returns (status, waited_ms) without raising (ZETA_ERR_TIMEOUT = 6 expected)."""
+    w = ctypes.c_double(0.0)
+    st = LIB.zeta_selftest_wait(ctx, limit_ms, ctypes.byref(w))
+    return st, w.value

@@ -12,7 +12,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libzeta.so")
-SOURCES = ["zeta_host.cpp", "zeta_policy.cpp", "zeta_learn.cpp", "zeta_capi.cpp", "zeta_kernels.cu", "zeta_mlp.cu"]
+SOURCES = ["zeta_host.cpp", "zeta_policy.cpp", "zeta_learn.cpp", "zeta_capi.cpp", "zeta_kernels.cu", "zeta_mlp.cu",
+           "zeta_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -379,6 +379,11 @@ zeta_status zeta_autotune(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t cou
     return ZETA_OK;
 }
 
+zeta_status zeta_selftest_wait(zeta_ctx *ctx, uint32_t limit_ms, double *waited_ms) {
+    if (!ctx || limit_ms == 0 || limit_ms > 10000) return ZETA_ERR_ARG;
+    return wait_selftest(limit_ms, waited_ms, ctx->error);
+}
+
 zeta_status zeta_horner_device(zeta_ctx *ctx, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
                                const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
                                const uint64_t *q) {

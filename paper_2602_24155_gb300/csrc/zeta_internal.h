@@ -132,6 +132,8 @@ struct DeviceEngine;
 DeviceEngine *engine_create(int device, void *stream, std::string &err);
 void engine_destroy(DeviceEngine *e);
 int engine_sm_count(const DeviceEngine *e);
+// Bounded-wait self-test on the current device (zeta_selftest.cu).
+zeta_status wait_selftest(uint32_t limit_ms, double *waited_ms, std::string &err);
 zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
                        uint32_t block_threads, std::string &err, double *ms_device);
 // The same in three phases: upload (inputs become resident in device

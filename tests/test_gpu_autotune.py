@@ -62,3 +62,12 @@ def test_bad_block_threads_and_mixed_classes_are_rejected(ctx):
         z.zeta_charpoly(ctx, spec, block_threads=100)
     with pytest.raises(z.ZetaError):
         z.zeta_autotune(ctx, [spec, _instance("quartic_curve_f11", 0)])
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(ctx):
+    # failure detection without a GPU fault: a wait on a barrier nothing arrives on runs out after its limit
+    st, waited = z.zeta_selftest_wait(ctx, 200)
+    assert st == 6 and 200.0 <= waited < 5000.0
+    spec = _instance("quartic_curve_f11", 0)
+    P, _ = z.zeta_charpoly(ctx, spec, path="gemm")
+    assert P == ozeta.compute_zeta(*spec).P
