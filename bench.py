@@ -29,11 +29,10 @@ import zeta_inputs as zi  # noqa: E402
 
 METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
 
-# DRAM traffic of the executor from ncu captures of 456 quintics (profiles/k_execute_quintic_curves_456_full.md,
-# profiles/k_execute_quintic_curves_456_learned_full.md): bytes read + written per instance, per policy and path,
-# valid for this kernel source only.
-PROFILED_KERNEL_MD5 = "f80003cbc8a0591ab02e0beb0ed19c5f"
-PROFILED_DRAM_BYTES_PER_INSTANCE = {("p_chunk", "vector"): 6.91e9 / 456, ("learned", "vector"): 5.71e9 / 456}
+# DRAM traffic of the executor from one ncu capture of 456 quintics (profiles/k_execute_quintic_curves_456_learned_full.md):
+# bytes read + written per instance, per policy and path, valid for this kernel source only.
+PROFILED_KERNEL_MD5 = "4e40aabe96c853fa1ceb94d9b557d8c7"
+PROFILED_DRAM_BYTES_PER_INSTANCE = {("learned", "vector"): (2.32326e9 + 2.15558e9) / 456}
 WORKLOAD = "quintic_curves"
 
 
