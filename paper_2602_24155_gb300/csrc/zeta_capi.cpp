@@ -192,8 +192,23 @@ struct zeta_batch_plan {
 
 extern "C" {
 
+}  // extern "C"
+
+// zeta_batch_prepare on a given lane of the engine (0: the context's stream, 1: the engine's second stream).
+static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                                      int lane, zeta_batch_plan **out);
+
+extern "C" {
+
 zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
                                zeta_batch_plan **out) {
+    return batch_prepare_lane(ctx, hs, count, opt, 0, out);
+}
+
+}  // extern "C"
+
+static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
+                                      int lane, zeta_batch_plan **out) {
     if (!ctx || !out || (!hs && count)) return ZETA_ERR_ARG;
     *out = nullptr;
     zeta_batch_plan *P = new (std::nothrow) zeta_batch_plan();
@@ -212,13 +227,15 @@ zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_
     P->ms_setup = now_ms() - t0;
     if (!P->ok.empty()) {
         resolve_path(ctx, P->ok, P->opt);
-        zeta_status st =
-            engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, P->opt.block_threads, &P->dev, ctx->error);
+        zeta_status st = engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, P->opt.block_threads, lane,
+                                        &P->dev, ctx->error);
         if (st) { delete P; return st; }
     }
     *out = P;
     return ZETA_OK;
 }
+
+extern "C" {
 
 zeta_status zeta_batch_run(zeta_ctx *ctx, zeta_batch_plan *P) {
     if (!ctx || !P) return ZETA_ERR_ARG;
@@ -284,13 +301,15 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
                        int64_t *P_out, size_t stride, zeta_stats *per_instance, zeta_stats *total) {
     if (!ctx || (!hs && count) || (!P_out && count)) return ZETA_ERR_ARG;
     // Pipelined: the host setup of sub-batch i+1 runs while the GPU reduces
-    // sub-batch i (kernel launches are asynchronous on the context stream).
-    const size_t S = count >= 256 ? 4 : 1;
+    // sub-batch i (launches are asynchronous), and consecutive sub-batches
+    // alternate between two streams so that the next persistent launch fills
+    // the SMs the previous one's tail leaves idle.
+    const size_t S = count >= 2048 ? 8 : count >= 256 ? 4 : 1;
     std::vector<zeta_batch_plan *> plans(S, nullptr);
     zeta_status st = ZETA_OK;
     for (size_t i = 0; i < S && !st; i++) {
         const size_t a = count * i / S, b = count * (i + 1) / S;
-        st = zeta_batch_prepare(ctx, hs + a, b - a, opt, &plans[i]);
+        st = batch_prepare_lane(ctx, hs + a, b - a, opt, (int)(i & 1), &plans[i]);
         if (!st) st = zeta_batch_run(ctx, plans[i]);
     }
     zeta_stats agg;

@@ -140,8 +140,11 @@ zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_pol
 // memory), launch (kernels only, asynchronous on the engine's stream),
 // collect (synchronise and read H back).
 struct DeviceBatch;
+// lane 0: the engine's stream; lane 1: a second, non-blocking stream, so that
+// consecutive batches overlap (the next launch's blocks take the SMs the
+// previous launch's tail leaves idle).
 zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
-                           uint32_t block_threads, DeviceBatch **out, std::string &err);
+                           uint32_t block_threads, int lane, DeviceBatch **out, std::string &err);
 zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err);
 zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err);
 void engine_release(DeviceBatch *B);

@@ -690,6 +690,7 @@ struct DevBuf {
 struct DeviceEngine {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // second lane for pipelined sub-batches (non-blocking, created on first use)
     int sms = 0;
     std::map<std::string, DevBuf> bufs;
     bool binom_ready = false;
@@ -750,6 +751,7 @@ int engine_sm_count(const DeviceEngine *e) { return e ? e->sms : 0; }
 void engine_destroy(DeviceEngine *e) {
     if (!e) return;
     cudaSetDevice(e->device);
+    if (e->side) cudaStreamDestroy(e->side);
     for (auto &kv : e->bufs)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
     delete e;
@@ -813,6 +815,7 @@ static void host_monos(int nv, int deg, std::vector<int> &out) {
 }
 
 struct DeviceBatch {
+    cudaStream_t stream = nullptr;  // the lane every upload, launch and download of this batch uses
     std::vector<Instance *> insts;
     zeta_policy policy;
     zeta_path path;
@@ -861,7 +864,8 @@ template <typename T>
 static zeta_status dev_upload(DeviceEngine *e, DeviceBatch *B, const std::vector<T> &v, T **out, std::string &err) {
     zeta_status st = dev_alloc(B, v.size(), out, err);
     if (st) return st;
-    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, e->stream));
+    (void)e;
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, B->stream));
     B->bytes_h2d += sizeof(T) * v.size();
     return ZETA_OK;
 }
@@ -887,13 +891,15 @@ void engine_batch_timing(const DeviceBatch *B, double *ms_kernel, uint64_t *laun
 }
 
 zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta_policy policy, zeta_path path,
-                           uint32_t block_threads, DeviceBatch **out, std::string &err) {
+                           uint32_t block_threads, int lane, DeviceBatch **out, std::string &err) {
     *out = nullptr;
     CUDA_TRY(cudaSetDevice(e->device));
     zeta_status st = upload_binom(e, err);
     if (st) return st;
+    if (lane && !e->side) CUDA_TRY(cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking));
     DeviceBatch *B = new (std::nothrow) DeviceBatch();
     if (!B) return ZETA_ERR_OOM;
+    B->stream = lane ? e->side : e->stream;
     B->insts = batch;
     B->policy = policy;
     B->path = path;
@@ -1117,9 +1123,9 @@ zeta_status engine_launch(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaEventCreate(&ev0));
     CUDA_TRY(cudaEventCreate(&ev1));
     B->events.push_back({ev0, ev1});
-    CUDA_TRY(cudaEventRecord(ev0, e->stream));
-    CUDA_TRY(cudaGraphLaunch(B->graph_exec, e->stream));
-    CUDA_TRY(cudaEventRecord(ev1, e->stream));
+    CUDA_TRY(cudaEventRecord(ev0, B->stream));
+    CUDA_TRY(cudaGraphLaunch(B->graph_exec, B->stream));
+    CUDA_TRY(cudaEventRecord(ev1, B->stream));
     return ZETA_OK;
 }
 
@@ -1127,9 +1133,9 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     CUDA_TRY(cudaSetDevice(e->device));
     std::vector<uint64_t> hH(B->h_stride * B->insts.size());
     unsigned long long hc[8] = {0};
-    CUDA_TRY(cudaMemcpyAsync(hH.data(), B->d_H, sizeof(uint64_t) * hH.size(), cudaMemcpyDeviceToHost, e->stream));
-    CUDA_TRY(cudaMemcpyAsync(hc, B->d_counters, sizeof(hc), cudaMemcpyDeviceToHost, e->stream));
-    CUDA_TRY(cudaStreamSynchronize(e->stream));
+    CUDA_TRY(cudaMemcpyAsync(hH.data(), B->d_H, sizeof(uint64_t) * hH.size(), cudaMemcpyDeviceToHost, B->stream));
+    CUDA_TRY(cudaMemcpyAsync(hc, B->d_counters, sizeof(hc), cudaMemcpyDeviceToHost, B->stream));
+    CUDA_TRY(cudaStreamSynchronize(B->stream));
     B->bytes_d2h = sizeof(uint64_t) * hH.size();
     B->ms_kernel = 0;
     B->launches = 0;
@@ -1170,7 +1176,7 @@ zeta_status engine_run(DeviceEngine *e, std::vector<Instance *> &batch, zeta_pol
     CUDA_TRY(cudaEventCreate(&ev1));
     CUDA_TRY(cudaEventRecord(ev0, e->stream));
     DeviceBatch *B = nullptr;
-    zeta_status st = engine_prepare(e, batch, policy, path, block_threads, &B, err);
+    zeta_status st = engine_prepare(e, batch, policy, path, block_threads, 0, &B, err);
     if (!st) st = engine_launch(e, B, err);
     if (!st) st = engine_collect(e, B, err);
     cudaEventRecord(ev1, e->stream);
