@@ -31,8 +31,8 @@ METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs 
 
 # DRAM traffic of the executor from one ncu capture of 456 quintics (profiles/k_execute_quintic_curves_456_learned_full.md):
 # bytes read + written per instance, per policy and path, valid for this kernel source only.
-PROFILED_KERNEL_MD5 = "4e40aabe96c853fa1ceb94d9b557d8c7"
-PROFILED_DRAM_BYTES_PER_INSTANCE = {("learned", "vector"): (2.32326e9 + 2.15558e9) / 456}
+PROFILED_KERNEL_MD5 = "d7643180187e994c67791777122feaeb"
+PROFILED_DRAM_BYTES_PER_INSTANCE = {("learned", "vector"): (2.281723e9 + 2.130924e9) / 456}
 WORKLOAD = "quintic_curves"
 
 
