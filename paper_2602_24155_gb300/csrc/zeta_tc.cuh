@@ -39,6 +39,9 @@
 // With c <= 8 the MMAs of a step are issued as two sets (diagonals below and
 // above an even split point) with two commits; warps 0-3 fold the first set
 // while the tensor core computes the second, and warps 4-7 fold the second.
+// Measured on plane quintics (s = 45) the overlap hides little: the CUDA-core
+// fold, reduction and digit writes take about 1.7 times the MMA issue and
+// wait, and the sum of the two is what a step costs.
 //
 // Requirements: s <= 64 (2s operand rows in one M = 128 tile), c <= 16,
 // q odd in [3, 2^60]; 256 threads; every wait on an MMA completion barrier
@@ -80,7 +83,7 @@ struct TcState {
     uint64_t da0, db0;  // descriptors of the A operand and of the first digit buffer
 };
 
-// Shared-memory bytes of the two operands for the largest L and cp, and of
+// Shared-memory bytes of the two operands for the largest L, and of
 // the 128 x 8 partial residues exchanged between the warp groups.
 __host__ __device__ inline size_t tc_operand_bytes(int s) {
     const int sK = tc_sK(s);
