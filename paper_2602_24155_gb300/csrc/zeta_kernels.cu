@@ -152,23 +152,33 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
     const int ngroups = cs / 4;
     const int items = s * ngroups;
     const uint32_t MASK20 = (1u << 20) - 1, MASK30 = (1u << 30) - 1;
+    // Few items (narrow W): split each item's j range between lanes l and
+    // l + 16 of a warp and add the two partial sums with one shuffle round,
+    // so that twice as many lanes work.  Block-uniform.
+    const bool jsplit = 2 * items <= (int)blockDim.x;
+    const int half = (int)((threadIdx.x >> 4) & 1u);
     int cur = 0;
     for (int step = 0; step < k; step++) {
         const uint2 *in = cur ? V : W;
         uint2 *out = cur ? W : V;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int r = it % s;
-            const int c0 = (it / s) * 4;
+        for (int base = 0; base < items; base += jsplit ? items : (int)blockDim.x) {
+            const int it = jsplit ? (int)((threadIdx.x >> 5) * 16 + (threadIdx.x & 15)) : base + (int)threadIdx.x;
+            const bool valid = it < items;
+            if (!jsplit && !valid) break;
+            const int r = valid ? it % s : 0;
+            const int c0 = valid ? (it / s) * 4 : 0;
+            const int jb = (jsplit && half) ? s / 2 : 0;
+            const int je = !valid ? jb : ((jsplit && !half) ? s / 2 : s);
             uint64_t S[4][6];
 #pragma unroll
             for (int cc = 0; cc < 4; cc++)
 #pragma unroll
                 for (int t = 0; t < 6; t++) S[cc][t] = 0;
-            const uint64_t *mp = Ms + r;
-            const uint4 *wp = reinterpret_cast<const uint4 *>(in + c0);
             const int wstride = cs / 2;  // uint4 per W row
+            const uint64_t *mp = Ms + (size_t)jb * s + r;
+            const uint4 *wp = reinterpret_cast<const uint4 *>(in + c0) + (size_t)jb * wstride;
 #pragma unroll 2
-            for (int j = 0; j < s; j++) {
+            for (int j = jb; j < je; j++) {
                 const uint64_t m = *mp;
                 mp += s;
                 const uint32_t m0 = (uint32_t)m & MASK20;
@@ -188,6 +198,13 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
                 madw(S[3][0], m0, wb.z); madw(S[3][1], m0, wb.w);
                 madw(S[3][2], m1, wb.z); madw(S[3][3], m1, wb.w);
                 madw(S[3][4], m2, wb.z); madw(S[3][5], m2, wb.w);
+            }
+            if (jsplit) {
+#pragma unroll
+                for (int cc = 0; cc < 4; cc++)
+#pragma unroll
+                    for (int t = 0; t < 6; t++) S[cc][t] += __shfl_xor_sync(0xffffffffu, S[cc][t], 16);
+                if (!valid || half) continue;
             }
             uint2 res[4];
 #pragma unroll
@@ -318,7 +335,7 @@ __host__ __device__ inline size_t chain_smem(int s, int c, int h_rows) {
 // the next phase, or accumulate x^U g / x^S into H at pole order n.  One
 // block owns an instance, so merges need no atomics.
 template <int CPT, bool MSMEM, bool TC>
-__global__ void __launch_bounds__(TC ? kTcThreads : 512) k_execute(
+__global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 96) k_execute(
     const DInst *__restrict__ insts, const DTab *__restrict__ tabs, const int32_t *__restrict__ tabpool,
     const uint64_t *__restrict__ secpool, const DChain *__restrict__ chains, const Term *__restrict__ terms,
     const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
