@@ -379,6 +379,22 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
                       uint64_t *sec, int32_t *chain_U, uint32_t *chain_terms, uint32_t *term_rc,
                       uint64_t *term_coeff, uint64_t *fin);
 
+/* The moves of the plan the host scheduled for one instance (host only, no
+ * device): the device executes exactly these.  Two calls: with NULL buffers
+ * it returns the counts, then fills caller-owned buffers.
+ *  phase_begin: nphases + 1 uint32, entries of phase f are [phase_begin[f],
+ *    phase_begin[f+1]).
+ *  entries: nentries x (nv + 7) int32: U[nv], chunk_begin, chunk_end (into
+ *    chunks), arrival (block of the previous phase whose sum starts W, or -1),
+ *    start_chain (chain of zeta_plan whose terms are added, or -1), dest
+ *    (block of the next phase the result is added to; -1 = pole order n,
+ *    accumulated into the numerators), flags (bit 0: first contribution to its
+ *    block: store instead of add), live (bit mask of the columns it carries).
+ *  chunks: nchunks x (nv + 1) int32: v[nv], k.
+ * Every plan passes the library's move check before it is returned. */
+zeta_status zeta_plan_moves(const zeta_hypersurface *hs, const zeta_options *opt, size_t *nphases, size_t *nentries,
+                            size_t *nchunks, uint32_t *phase_begin, int32_t *entries, int32_t *chunks);
+
 /* Host finishing steps from accumulated pole-order-n numerators:
  *  H: h_rows x b uint64 mod q -- column j holds the sum over all reduced
  *     terms of column j of the numerators x^U g / x^S (degree dn-n-1).

@@ -30,7 +30,7 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
-           "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait"]
+           "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait", "zeta_plan_moves"]
 FLAG_Y_ONLY = 1
 
 
@@ -135,6 +135,8 @@ def _load():
     lib.zeta_batch_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_size_t,
                                       P(Stats), P(Stats)]
     lib.zeta_batch_release.argtypes = [ctypes.c_void_p]
+    lib.zeta_plan_moves.argtypes = [P(Hypersurface), P(Options), P(ctypes.c_size_t), P(ctypes.c_size_t),
+                                    P(ctypes.c_size_t), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
     lib.zeta_autotune.argtypes = [ctypes.c_void_p, P(Hypersurface), ctypes.c_size_t, P(Options), ctypes.c_uint32,
                                   P(Tuning)]
@@ -479,3 +481,20 @@ def zeta_selftest_wait(ctx, limit_ms):
     w = ctypes.c_double(0.0)
     st = LIB.zeta_selftest_wait(ctx, limit_ms, ctypes.byref(w))
     return st, w.value
+
+
+def zeta_plan_moves(spec, **opt):
+    """The scheduled moves of one instance (host only): dict with 'phase_begin', 'entries' (rows of
+    U[nv], chunk_begin, chunk_end, arrival, start_chain, dest, flags, live) and 'chunks' (rows of v[nv], k)."""
+    hs = _hypersurface(spec)
+    o = _options(**opt)
+    npha, nent, nchk = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(None, LIB.zeta_plan_moves(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(npha), ctypes.byref(nent),
+                                     ctypes.byref(nchk), None, None, None))
+    nv = spec[0] + 1
+    ph = np.zeros(npha.value + 1, dtype=np.uint32)
+    ent = np.zeros((nent.value, nv + 7), dtype=np.int32)
+    chk = np.zeros((max(nchk.value, 1), nv + 1), dtype=np.int32)
+    _check(None, LIB.zeta_plan_moves(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(npha), ctypes.byref(nent),
+                                     ctypes.byref(nchk), ph.ctypes.data, ent.ctypes.data, chk.ctypes.data))
+    return {"phase_begin": ph, "entries": ent, "chunks": chk[:nchk.value]}

@@ -447,6 +447,44 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
     return ZETA_OK;
 }
 
+zeta_status zeta_plan_moves(const zeta_hypersurface *hs, const zeta_options *opt, size_t *nphases, size_t *nentries,
+                            size_t *nchunks, uint32_t *phase_begin, int32_t *entries, int32_t *chunks) {
+    if (!hs || !nphases || !nentries || !nchunks) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    X.net.w = o.policy_weights;
+    X.net.hidden = (int)o.policy_hidden;
+    zeta_status st = prepare_instance(hs, &o, true, X);
+    if (!st) st = schedule_policy(X, o.policy);
+    if (st) return st;
+    const Plan &P = X.plan;
+    const size_t nv = X.nv;
+    *nphases = P.phase_begin.size() - 1;
+    *nentries = P.entries.size();
+    *nchunks = P.chunks.size();
+    if (phase_begin) std::memcpy(phase_begin, P.phase_begin.data(), sizeof(uint32_t) * P.phase_begin.size());
+    if (entries)
+        for (size_t i = 0; i < P.entries.size(); i++) {
+            const PlanEntry &e = P.entries[i];
+            int32_t *o_ = entries + i * (nv + 7);
+            for (size_t t = 0; t < nv; t++) o_[t] = e.U[t];
+            o_[nv] = (int32_t)e.chunk_begin;
+            o_[nv + 1] = (int32_t)e.chunk_end;
+            o_[nv + 2] = e.arrival;
+            o_[nv + 3] = e.start_chain;
+            o_[nv + 4] = e.dest;
+            o_[nv + 5] = (int32_t)e.flags;
+            o_[nv + 6] = (int32_t)e.live;
+        }
+    if (chunks)
+        for (size_t i = 0; i < P.chunks.size(); i++) {
+            int32_t *o_ = chunks + i * (nv + 1);
+            for (size_t t = 0; t < nv; t++) o_[t] = P.chunks[i].v[t];
+            o_[nv] = P.chunks[i].k;
+        }
+    return ZETA_OK;
+}
+
 zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options *opt, size_t *ngroups, size_t *ncand,
                                 float *X, uint32_t *group_off, uint32_t *labels, int32_t *costs) {
     if (!hs || !ngroups || !ncand) return ZETA_ERR_ARG;

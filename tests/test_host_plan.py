@@ -143,3 +143,126 @@ def test_cover_policy_plays_fewer_column_steps_with_valid_plans():
     a = z.zeta_plan((n, d, p, c), policy="cover", r=1)["game"]
     b = z.zeta_plan((n, d, p, c), policy="p_chunk", r=1)["game"]
     assert a["column_steps"] == b["column_steps"]
+
+
+def _step_matrices(spec, plan, U, v, k):
+    """A and B of a chunk of k steps from U in direction v (M(y) = yA + B for u = x + y v, x = U - k v), generated
+    from the exported section by the monomial formula."""
+    n, d, p, coeffs = spec
+    nv = n + 1
+    q = int(plan["q"])
+    mS = monomials(nv, d * n - n)
+    s = len(mS)
+    src = _rank_table(nv, n * (d - 2))
+    kap = _rank_table(nv, (n + 1) * (d - 2) + 1)
+    nsrc = len(src)
+    sec = plan["sec"]
+    x = tuple(a - k * bb for a, bb in zip(U, v))
+    A = np.zeros((s, s), dtype=object)
+    B = np.zeros((s, s), dtype=object)
+    for j, mu in enumerate(mS):
+        g = tuple(v[t] + mu[t] - 1 for t in range(nv))
+        if min(g) < 0:
+            continue
+        col = kap[g]
+        for r, om in enumerate(mS):
+            a = bb = 0
+            for i in range(nv):
+                nu = tuple(om[t] - 1 + (1 if t == i else 0) for t in range(nv))
+                if min(nu) < 0:
+                    continue
+                val = int(sec[i * nsrc + src[nu], col])
+                a += v[i] * val
+                bb += (x[i] + om[i]) * val
+            A[r, j] = a % q
+            B[r, j] = bb % q
+    return A, B, x
+
+
+def replay_moves(spec, plan, moves):
+    """The device executor's semantics in plain Python: phase by phase, every entry starts from its arrival block
+    and/or its start chain, plays its chunks (Algorithm 2), then is stored or added into its destination block of
+    the next phase, or accumulated into the numerators at pole order n."""
+    n, d, p, coeffs = spec
+    nv = n + 1
+    q = int(plan["q"])
+    b = plan["b"]
+    mS = monomials(nv, d * n - n)
+    s = len(mS)
+    hpos = _rank_table(nv, d * n - n - 1)
+    H = np.zeros((len(hpos), b), dtype=object)
+    ph, ent, chk = moves["phase_begin"], moves["entries"], moves["chunks"]
+    cur = {}
+    cache = {}
+    for f in range(len(ph) - 1):
+        nxt = {}
+        for ei in range(int(ph[f]), int(ph[f + 1])):
+            row = [int(x) for x in ent[ei]]
+            U = tuple(row[:nv])
+            c0, c1, arrival, start, dest, flags, live = row[nv:nv + 7]
+            W = cur[arrival].copy() if arrival >= 0 else np.zeros((s, b), dtype=object)
+            if start >= 0:
+                t0, t1 = plan["chain_terms"][start]
+                for t in range(int(t0), int(t1)):
+                    r, c = plan["term_rc"][t]
+                    W[r, c] = (W[r, c] + int(plan["term_coeff"][t])) % q
+            for ci in range(c0, c1):
+                v = tuple(int(x) for x in chk[ci][:nv])
+                k = int(chk[ci][nv])
+                key = (U, v, k)
+                if key not in cache:
+                    cache[key] = _step_matrices(spec, plan, U, v, k)
+                A, B, x = cache[key]
+                W = ozeta.horner_python(A, B, W, k, q)
+                U = x
+            assert all((live >> c) & 1 or not W[:, c].any() for c in range(b))
+            if dest < 0:
+                assert sum(U) == n
+                for j, mu in enumerate(mS):
+                    g = tuple(U[t] + mu[t] - 1 for t in range(nv))
+                    if min(g) < 0:
+                        continue
+                    H[hpos[g]] = (H[hpos[g]] + W[j]) % q
+            elif flags & 1:
+                nxt[dest] = W
+            else:
+                nxt[dest] = (nxt[dest] + W) % q
+        cur = nxt
+    return H.astype(np.uint64)
+
+
+@pytest.mark.parametrize("policy", ["p_chunk", "cover", "var_by_var", "learned"])
+def test_replayed_moves_of_every_policy_match_oracle(policy):
+    """The exact moves the device would execute (zeta_plan_moves), replayed with exact arithmetic: Y, F and P(T)
+    equal the oracle's for the paper's policies, the cover search and the learned policy (a network with random
+    weights still yields a legal plan)."""
+    n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
+    spec = (n, d, p, c)
+    opt = {"policy": policy}
+    if policy == "learned":
+        opt.update(weights=z.zeta_mlp_init(8, 3), hidden=8)
+    plan = z.zeta_plan(spec, **opt)
+    moves = z.zeta_plan_moves(spec, **opt)
+    assert len(moves["entries"]) == plan["game"]["entries"]
+    H = replay_moves(spec, plan, moves)
+    F, Y, P = z.zeta_finish(spec, H)
+    res = ozeta.compute_zeta(n, d, p, c)
+    assert (Y.astype(object) == res.Y).all()
+    assert P == res.P
+
+
+@pytest.mark.parametrize("policy", ["cover", "learned"])
+def test_replayed_moves_on_a_quintic_at_precision_one(policy):
+    # a non-ordinary plane quintic over F_7 at relative precision 1 (P mod p): the cover levels have freedom d - 3 = 2
+    n, d, p, c, _ = zi.draw_instance("quintic_curves", 12, cohomology.is_smooth)
+    spec = (n, d, p, c)
+    opt = {"policy": policy, "r": 1}
+    if policy == "learned":
+        opt.update(weights=z.zeta_mlp_init(8, 5), hidden=8)
+    plan = z.zeta_plan(spec, **opt)
+    moves = z.zeta_plan_moves(spec, **opt)
+    H = replay_moves(spec, plan, moves)
+    F, Y, P = z.zeta_finish(spec, H, r=1)
+    res = ozeta.compute_zeta(n, d, p, c, r=1)
+    assert (Y.astype(object) == res.Y).all()
+    assert [a % p for a in P] == [a % p for a in res.P]
