@@ -28,8 +28,9 @@
  *    (columns in the order above).  Basis order: m ascending, then monomial
  *    order.  b = dim = ((d-1)^{n+1} + (-1)^{n+1}(d-1)) / d.
  *  - Supported: S = {0..n} controlled reduction (Prop. 3.3), which needs
- *    d >= n+1; p^M < 2^63.  Other inputs return ZETA_ERR_UNSUPPORTED or
- *    ZETA_ERR_PRECISION.
+ *    d >= n+1; p^M < 2^60 (the device keeps residues as two 30-bit limbs, or
+ *    as at most eight balanced base-256 digits on the tensor cores).  Other
+ *    inputs return ZETA_ERR_UNSUPPORTED or ZETA_ERR_PRECISION.
  *  - Calls are synchronous: they return after the device work has finished.
  *    One context must not be used from two host threads at once.
  */
@@ -48,7 +49,7 @@ typedef enum {
     ZETA_ERR_ARG = 1,          /* null pointer, bad size, coefficient out of range */
     ZETA_ERR_NOT_SMOOTH = 2,   /* the Jacobian criterion fails (Sec. 2.1, Def. 3.1) */
     ZETA_ERR_UNSUPPORTED = 3,  /* p < 7, p >= 50, p | d, p <= n, or d < n+1 */
-    ZETA_ERR_PRECISION = 4,    /* p^M would not fit below 2^63 */
+    ZETA_ERR_PRECISION = 4,    /* p^M would not fit below 2^60 */
     ZETA_ERR_DEVICE = 5,       /* CUDA error or no usable device */
     ZETA_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
     ZETA_ERR_OOM = 7,          /* host or device allocation failed */
@@ -178,8 +179,10 @@ zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta
                           int64_t *P_out, zeta_stats *st);
 
 /* Many hypersurfaces (any mix of n, d, p).  Batches of 256 or more are split
- * into four sub-batches whose host setup overlaps the device work of the
- * previous one (one device pass each).
+ * into four sub-batches (eight from 2048) whose host setup overlaps the device
+ * work of the previous one; consecutive sub-batches alternate between the
+ * context's stream and a second stream of the context, so that their
+ * persistent launches overlap.
  *  P_out: count * stride * 2 int64; instance i writes b_i+1 coefficients
  *         (two words each, as in zeta_charpoly) at P_out + 2*i*stride
  *         (stride >= max b_i + 1).
@@ -242,7 +245,8 @@ zeta_status zeta_autotune(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t cou
  *  For problem t: W_t <- M(0) M(1) ... M(k_t - 1) W_t mod q_t with
  *  M(y) = y A_t + B_t; A_t, B_t are s x s row-major at A + t*s*s, B + t*s*s;
  *  W_t is s x c row-major at W + t*s*c (overwritten); k_t = k[t] >= 0;
- *  q_t = q[t] in [2, 2^63).  Entries must be reduced mod q_t.
+ *  q_t = q[t] odd in [3, 2^60] with s < 8 q_t (ZETA_ERR_ARG otherwise).
+ *  Entries must be reduced mod q_t.
  *  All pointers are device pointers; ZETA_ERR_ARG if s or c exceed the
  *  kernel limits (s <= 512, c <= 32; with ZETA_PATH_GEMM s <= 64, c <= 16).
  *  ZETA_ERR_TIMEOUT if a tensor-core step did not complete within 2 s (the

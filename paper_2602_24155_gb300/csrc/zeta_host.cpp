@@ -412,7 +412,9 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
         Mp = std::max(Mp, (int)X.rm[m - 1] + vp_factorial((uint64_t)p * sm - 1, p) - (int)m + 1);
     }
     X.M = (uint32_t)Mp;
-    if (!pow_fits(p, X.M, (uint64_t)1 << 63, &X.q)) { X.error = "p^M exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
+    // the device keeps residues mod q as two 30-bit limbs (vector path) or at most
+    // eight balanced base-256 digits (tensor-core path): q < 2^60
+    if (!pow_fits(p, X.M, (uint64_t)1 << 60, &X.q)) { X.error = "p^M exceeds 2^60"; return X.status = ZETA_ERR_PRECISION; }
     for (uint32_t m = 1; m <= n; m++) {
         uint64_t tmp;
         if (X.N[m - 1] && !pow_fits(p, X.N[m - 1] + m - 1, (uint64_t)1 << 63, &tmp)) { X.error = "p^s exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }

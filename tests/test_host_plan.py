@@ -266,3 +266,18 @@ def test_replayed_moves_on_a_quintic_at_precision_one(policy):
     res = ozeta.compute_zeta(n, d, p, c, r=1)
     assert (Y.astype(object) == res.Y).all()
     assert [a % p for a in P] == [a % p for a in res.P]
+
+
+def test_moduli_above_2_60_are_rejected():
+    """The device keeps residues as two 30-bit limbs (and at most eight balanced base-256 digits on the tensor
+    cores): a plane quintic over F_37 at relative precision 6 needs p^M = 37^12 = 2^62.5 and is refused before any
+    device work, while its default precision (below 2^60) is accepted."""
+    import zeta_inputs as zi
+    from oracle import cohomology
+    n, d, p, c, _ = zi.draw_instance("quintic_curves", 8, cohomology.is_smooth)
+    assert p == 37
+    b, r, M, s = z.zeta_query((n, d, p, c))
+    assert p ** M < 2 ** 60
+    with pytest.raises(z.ZetaError) as err:
+        z.zeta_query((n, d, p, c), r=6)
+    assert err.value.status == 4
