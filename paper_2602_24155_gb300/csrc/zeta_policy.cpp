@@ -129,6 +129,7 @@ void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live
         for (int t = 0; t < nv; t++) v[t] = 1;
         for (int u = 0; u < x; u++) {
             while (cur < nv && rem[cur] == 0) cur++;
+            if (cur >= nv) break;  // cannot happen (the units sum to x L); validate_plan rejects the plan
             v[cur]++;
             rem[cur]--;
         }
