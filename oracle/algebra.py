@@ -110,10 +110,16 @@ def right_inverse_mod(M, q, p):
     and the pivot is the first remaining row whose entry is a unit; free
     variables are set to zero.  Returns (X, pivot_columns) with X a
     cols x rows object array.  Raises ValueError if the rank mod p is short.
+    When q^2 < 2^62 the same elimination runs in int64 (every product of two
+    residues is exact there); otherwise in Python integers.
     """
     A = np.array(M, dtype=object) % q
     r, c = A.shape
-    E = np.zeros((r, r), dtype=object)
+    small = q * q < (1 << 62)
+    dt = np.int64 if small else object
+    if small:
+        A = A.astype(np.int64)
+    E = np.zeros((r, r), dtype=dt)
     for i in range(r):
         E[i, i] = 1
     aug = np.concatenate([A, E], axis=1)
@@ -143,7 +149,7 @@ def right_inverse_mod(M, q, p):
         raise ValueError("matrix is not of full row rank mod p")
     X = np.zeros((c, r), dtype=object)
     for k, col in enumerate(pivcols):
-        X[col, :] = aug[k, c:]
+        X[col, :] = [int(a) for a in aug[k, c:]]
     return X, pivcols
 
 

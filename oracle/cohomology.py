@@ -2,7 +2,19 @@
 
 Follows Sec. 2.2-2.3 (Griffiths-Dwork relations, monomial basis of the
 cokernel of the Jacobian map M_k), Prop. 3.3 (the controlled-reduction map
-R_{u,v} for S = {0..n}) and Sec. 3.3 step (2) (final reduction to the basis).
+R_{u,v}, for S = {0..n} and for a general S with f S-smooth, Definition 3.1)
+and Sec. 3.3 step (2) (final reduction to the basis).
+
+General S.  With J_S spanned by d_i f (i in S) and x_i d_i f (i not in S),
+Prop. 3.3 writes x^v g / x^S = sum_{i in S} g_i d_i f + sum_{i not in S}
+x_i g_i d_i f.  Put G_i = g_i for i in S and G_i = x_i g_i otherwise (a form
+of degree kappa_S - d + 1, divisible by x_i when i is not in S); then both
+sums of the printed R_{u,v} become x^S sum_i (u_i G_i / x_i + d_i G_i), and
+a monomial x^nu of G_i with coefficient c contributes (u_i + nu_i) c to the
+output monomial nu + 1_S - e_i.  kappa_S = deg(x^v g / x^S) = d + dn - n - |S|
+= (n+1)(d-1) + 1 - |S|, the Macaulay degree of the n+1 generators of J_S
+(|S| of degree d-1, the rest of degree d), so the section exists exactly
+when f is S-smooth.  S = {0..n} is the smooth case of the same formulas.
 """
 import numpy as np
 
@@ -21,15 +33,18 @@ class Hypersurface:
         self.f = poly_from_coeffs(self.nv, d, coeffs)
         self.df = [poly_deriv(self.f, i) for i in range(self.nv)]
 
-    def jacobian_matrix(self, k):
+    def jacobian_matrix(self, k, S=None):
         """Matrix of M_k: (Homog_{k-d+1})^{n+1} -> Homog_k, (mu_i) -> sum mu_i d_i f.
 
         Rows: monomials of degree k; columns: pairs (i, nu) with i major and
-        nu in monomial order (Sec. 2.3).
+        nu in monomial order (Sec. 2.3).  With S given, the map of J_S
+        (Definition 3.1): for i not in S only the nu with nu_i >= 1 are
+        columns (the multiples of x_i d_i f).
         """
         rows = MonomialIndex(self.nv, k)
         src = monomials(self.nv, k - self.d + 1)
-        cols = [(i, nu) for i in range(self.nv) for nu in src]
+        S = range(self.nv) if S is None else S
+        cols = [(i, nu) for i in range(self.nv) for nu in src if i in S or nu[i] >= 1]
         M = [[0] * len(cols) for _ in range(len(rows))]
         for c, (i, nu) in enumerate(cols):
             for e, a in self.df[i].items():
@@ -48,6 +63,29 @@ def is_smooth(n, d, p, coeffs):
     X = Hypersurface(n, d, p, coeffs)
     k = (n + 1) * (d - 2) + 1
     M, rows, _ = X.jacobian_matrix(k)
+    return len(pivot_columns_mod_p(M, p)) == len(rows)
+
+
+def full_S(n):
+    return tuple(range(n + 1))
+
+
+def kappa_S(n, d, S):
+    """Degree of x^v g / x^S in Prop. 3.3: d + dn - n - |S| = (n+1)(d-1) + 1 - |S|."""
+    return (n + 1) * (d - 1) + 1 - len(S)
+
+
+def is_S_smooth(n, d, p, coeffs, S):
+    """Definition 3.1: J_S defines the empty scheme, decided as for `is_smooth`.
+
+    The n+1 generators of J_S have no common projective zero iff they form a
+    regular sequence, iff their span contains every form of degree
+    kappa_S (Macaulay: the sum of the degrees minus n).  S = {0..n} gives
+    `is_smooth`.
+    """
+    X = Hypersurface(n, d, p, coeffs)
+    k = kappa_S(n, d, S)
+    M, rows, _ = X.jacobian_matrix(k, S)
     return len(pivot_columns_mod_p(M, p)) == len(rows)
 
 
@@ -83,20 +121,23 @@ def hodge_count(n, d):
 
 
 class Section:
-    """Right inverse of M_kappa over Z/q, kappa = (n+1)(d-2)+1 (Prop. 3.3 proof).
+    """Right inverse of the map of J_S in degree kappa_S over Z/q (Prop. 3.3 proof).
 
-    For a monomial x^gamma of degree kappa, `solve(gamma)` returns g_0..g_n in
-    Homog_{n(d-2)} with sum g_i d_i f = x^gamma mod q.  The decomposition is
+    For a monomial x^gamma of degree kappa_S, `solve(gamma)` returns
+    G_0..G_n with sum G_i d_i f = x^gamma mod q, G_i divisible by x_i for i
+    not in S (G_i = x_i g_i in the printed notation).  For S = {0..n},
+    kappa = (n+1)(d-2)+1 and G_i = g_i in Homog_{n(d-2)}.  The decomposition is
     not unique; this one is Gauss-Jordan with unit pivots, columns (i, nu)
     visited in order, free variables zero.  `column_order` lets a test pick a
     different convention to check that results do not depend on it.
     """
 
-    def __init__(self, X, q, column_order=None):
+    def __init__(self, X, q, column_order=None, S=None):
         self.X = X
         self.q = q
-        k = X.nv * (X.d - 2) + 1
-        M, rows, cols = X.jacobian_matrix(k)
+        self.S = full_S(X.n) if S is None else tuple(sorted(S))
+        k = kappa_S(X.n, X.d, self.S)
+        M, rows, cols = X.jacobian_matrix(k, self.S)
         if column_order is not None:
             M = [[row[c] for c in column_order] for row in M]
             cols = [cols[c] for c in column_order]
@@ -121,51 +162,55 @@ class Section:
 
 
 def R_matrix(X, sec, Sidx, u, v):
-    """Matrix of R_{u,v} on Homog_{dn-n} (Prop. 3.3 with S = {0..n}), mod q.
+    """Matrix of R_{u,v} on Homog_{dn-n} (Prop. 3.3), mod q, for the section's S.
 
-    For an input monomial x^mu: x^v x^mu / x^S = sum_i g_i d_i f via the
-    section, and R_{u,v}(x^mu) = x^S sum_i (u_i g_i + x_i d_i g_i) / x_i.
-    Inputs with v_i + mu_i = 0 for some i have no polynomial x^v x^mu / x^S;
-    they never carry a nonzero coefficient on a valid reduction path (their
-    column is left zero and the driver asserts the coefficient is zero).
+    For an input monomial x^mu: x^v x^mu / x^S = sum_i G_i d_i f via the
+    section, and R_{u,v}(x^mu) = x^S sum_i (u_i G_i / x_i + d_i G_i): the
+    monomial x^nu of G_i with coefficient a adds (u_i + nu_i) a at
+    nu + 1_S - e_i.  Inputs with x^v x^mu / x^S not a polynomial have no
+    image; they never carry a nonzero coefficient on a valid reduction path
+    (their column is left zero and the driver asserts the coefficient is zero).
     """
     q = sec.q
     s = len(Sidx)
     R = np.zeros((s, s), dtype=object)
-    one = (1,) * X.nv
+    oneS = tuple(1 if i in sec.S else 0 for i in range(X.nv))
     for c, mu in enumerate(Sidx.mons):
-        gamma = sub_exp(add_exp(v, mu), one)
+        gamma = sub_exp(add_exp(v, mu), oneS)
         if min(gamma) < 0:
             continue
-        g = sec.solve(gamma)
+        G = sec.solve(gamma)
         for i in range(X.nv):
-            # h_i = u_i g_i + x_i d_i g_i, then multiply by x^S / x_i
-            h = {}
-            for nu, a in g[i].items():
-                h[nu] = h.get(nu, 0) + u[i] * a
-            for nu, a in poly_deriv(g[i], i).items():
-                nu2 = nu[:i] + (nu[i] + 1,) + nu[i + 1:]
-                h[nu2] = h.get(nu2, 0) + a
-            for nu, a in h.items():
-                out = tuple(nu[t] + (0 if t == i else 1) for t in range(X.nv))
-                R[Sidx.pos[out], c] = (R[Sidx.pos[out], c] + a) % q
+            for nu, a in G[i].items():
+                out = tuple(nu[t] + oneS[t] - (1 if t == i else 0) for t in range(X.nv))
+                R[Sidx.pos[out], c] = (R[Sidx.pos[out], c] + (u[i] + nu[i]) * a) % q
     return R
 
 
 def affine_parts(X, sec, Sidx, v):
     """A_0..A_{n+1} with R_{u,v} = sum_i A_i u_i + A_{n+1} (Sec. 3.1).
 
-    R_{u,v} is affine in u by its definition, so A_{n+1} = R_{0,v} and
-    A_i = R_{e_i,v} - R_{0,v}.
+    R_{u,v} is affine in u by its definition (R_matrix): the monomial x^nu of
+    G_i with coefficient a puts a into A_i and nu_i a into A_{n+1}, both at
+    row nu + 1_S - e_i.
     """
     q = sec.q
-    zero = (0,) * X.nv
-    R0 = R_matrix(X, sec, Sidx, zero, v)
-    parts = []
-    for i in range(X.nv):
-        ei = tuple(1 if t == i else 0 for t in range(X.nv))
-        parts.append((R_matrix(X, sec, Sidx, ei, v) - R0) % q)
-    parts.append(R0)
+    s = len(Sidx)
+    parts = [np.zeros((s, s), dtype=object) for _ in range(X.nv + 1)]
+    A_last = parts[X.nv]
+    oneS = tuple(1 if i in sec.S else 0 for i in range(X.nv))
+    for c, mu in enumerate(Sidx.mons):
+        gamma = sub_exp(add_exp(v, mu), oneS)
+        if min(gamma) < 0:
+            continue
+        G = sec.solve(gamma)
+        for i in range(X.nv):
+            Ai = parts[i]
+            for nu, a in G[i].items():
+                row = Sidx.pos[tuple(nu[t] + oneS[t] - (1 if t == i else 0) for t in range(X.nv))]
+                Ai[row, c] = (Ai[row, c] + a) % q
+                if nu[i]:
+                    A_last[row, c] = (A_last[row, c] + nu[i] * a) % q
     return parts
 
 

@@ -3,7 +3,9 @@
 Sec. 3.1 Algorithm 1 (Tweak), Sec. 4 Algorithm 3 (greedy v), the abstract
 reduction game of Sec. 3.4 and the three policies of Sec. 4.1-4.3.
 Exponent vectors are tuples in N^{n+1}.  A term of pole order K has
-|u| = n + d (K - n) (its numerator is x^u g / x^S with g in Homog_{dn-n}).
+|u| = |S| - 1 + d (K - n): its numerator x^u g / x^S, g in Homog_{dn-n}, has
+degree dK - n - 1.  For S = {0..n} that is n + d (K - n); the game ends at
+|u| = |S| - 1 (pole order n).
 """
 
 
@@ -66,17 +68,20 @@ def in_V_full(u, v, k, S):
     return True
 
 
-def k_max(u, v, n, d):
-    """Largest k with u - k v >= 0 and |u - k v| >= n (Sec. 4.2)."""
-    k = (sum(u) - n) // d
+def k_max(u, v, n, d, base=None):
+    """Largest k with u - k v >= 0 and |u - k v| >= base (Sec. 4.2); base = |S| - 1,
+    n for S = {0..n}."""
+    base = n if base is None else base
+    k = (sum(u) - base) // d
     for i in range(len(u)):
         if v[i] > 0:
             k = min(k, u[i] // v[i])
     return k
 
 
-def pole_order(u, n, d):
-    return (sum(u) - n) // d + n
+def pole_order(u, n, d, base=None):
+    base = n if base is None else base
+    return (sum(u) - base) // d + n
 
 
 def sub_kv(u, v, k):
@@ -111,18 +116,20 @@ def merge_terms(terms, add, log):
 
 
 def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
-    """Run a policy on the initial term list; returns the terms at |u| = n.
+    """Run a policy on the initial term list; returns the terms at pole order n
+    (|u| = |S| - 1).
 
     reduce_chunk(u, v, k, payload) -> payload after k steps in direction v.
     add(a, b) -> merged payload.
     """
     S = set(S)
+    base = len(S) - 1
     if policy == "depth_first":
         out = []
         for u, w in terms:
-            while sum(u) > n:
+            while sum(u) > base:
                 v = greedy_v(d, u, S)
-                k = k_max(u, v, n, d)
+                k = k_max(u, v, n, d, base)
                 assert k >= 1 and in_V_full(u, v, k, S)
                 w = reduce_chunk(u, v, k, w)
                 u = sub_kv(u, v, k)
@@ -140,11 +147,11 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
             nxt = []
             for u, w in live:
                 if sum(u) == L:
-                    K = pole_order(u, n, d)
+                    K = pole_order(u, n, d, base)
                     left = K - max(K - p, n)
                     while left > 0:
                         v = greedy_v(d, u, S)
-                        k = min(left, k_max(u, v, n, d))
+                        k = min(left, k_max(u, v, n, d, base))
                         assert k >= 1 and in_V_full(u, v, k, S)
                         w = reduce_chunk(u, v, k, w)
                         u = sub_kv(u, v, k)
@@ -152,8 +159,8 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
                 nxt.append((u, w))
             # terms at pole order n leave the game (their numerators are summed
             # by the final reduction); the others are combined
-            done += [(u, w) for u, w in nxt if sum(u) == n]
-            live = merge_terms([(u, w) for u, w in nxt if sum(u) > n], add, log)
+            done += [(u, w) for u, w in nxt if sum(u) == base]
+            live = merge_terms([(u, w) for u, w in nxt if sum(u) > base], add, log)
         return done
     if policy == "var_by_var":
         live = merge_terms(terms, add, log)
@@ -161,16 +168,16 @@ def play(policy, terms, n, d, p, S, reduce_chunk, add, log):
         for t in range(n, -1, -1):
             nxt = []
             for u, w in live:
-                while sum(u) > n and u[t] > 0:
+                while sum(u) > base and u[t] > 0:
                     v = greedy_v(d, u, S)
-                    k = k_max(u, v, n, d)
+                    k = k_max(u, v, n, d, base)
                     assert k >= 1 and in_V_full(u, v, k, S)
                     w = reduce_chunk(u, v, k, w)
                     u = sub_kv(u, v, k)
                 nxt.append((u, w))
-            done += [(u, w) for u, w in nxt if sum(u) == n]
-            live = merge_terms([(u, w) for u, w in nxt if sum(u) > n], add, log)
-        # after the u_0 phase every term has |u| = n
+            done += [(u, w) for u, w in nxt if sum(u) == base]
+            live = merge_terms([(u, w) for u, w in nxt if sum(u) > base], add, log)
+        # after the u_0 phase every term has |u| = |S| - 1
         assert not live
         return done
     raise ValueError("unknown policy %r" % policy)

@@ -3,7 +3,8 @@
 The end-to-end computation of Sec. 2-4 on the CPU with exact integers:
   1. smoothness (Jacobian criterion), monomial basis B (Sec. 2.3)
   2. precision r, N_m, M (Sec. 2.5; readings in oracle.precision)
-  3. Frobenius expansion (Prop. 2.1): terms x^{p(beta+alpha+1)} / (x^S f^{p(m+j)})
+  3. Frobenius expansion (Prop. 2.1): terms x^gamma / (x^S f^{p(m+j)}),
+     gamma = p(beta+alpha+1) - 1 + 1_S
   4. Tweak (Alg. 1) into (u, g), terms with equal u combined
   5. a reduction policy (Sec. 4) plays the game of Sec. 3.4; each chunk is
      evaluated with Algorithm 2 on R_{x+yv,v} = y A + B (Prop. 3.3, Sec. 3.2)
@@ -30,7 +31,7 @@ import numpy as np
 
 from .algebra import MonomialIndex, poly_powers, berkowitz_charpoly, add_exp, sub_exp
 from .cohomology import (Hypersurface, cohomology_basis, hodge_count, is_smooth,
-                         Section, affine_parts, FinalReduction)
+                         is_S_smooth, full_S, Section, affine_parts, FinalReduction)
 from .policies import tweak, play, GameLog
 from .precision import Precision, vp_factorial, hodge_polygon
 
@@ -123,18 +124,21 @@ class ZetaResult:
     pass
 
 
-def frobenius_terms(X, basis, prec):
+def frobenius_terms(X, basis, prec, S=None):
     """Prop. 2.1 terms for every basis column, Tweak'd and scaled.
 
     Yields (col, U, J, coefficient mod q) where the term is
       coefficient * x^U x^J / (x^S f^{p(m+j)}),
     coefficient = (D_{j,m} C_{j,alpha} mod p^{s_m}) * (p s_m - 1)! / (p(m+j) - 1)!,
     the factor p^{m-1} of Prop. 2.1 left out (restored in the normalisation).
+    The numerator of Prop. 2.1 is x^{p(beta+alpha+1) - 1}; over x^S it is
+    x^gamma with gamma = p(beta+alpha+1) - 1 + 1_S (p(beta+alpha+1) for S = {0..n}).
     """
     n, d, p, q = X.n, X.d, X.p, prec.q
+    S = full_S(n) if S is None else S
+    oneS = tuple(1 if i in S else 0 for i in range(X.nv))
     jmax = max(prec.N.values())
     powers = poly_powers(X.f, jmax - 1)
-    one = (1,) * X.nv
     for col, (m, beta) in enumerate(basis):
         N, s = prec.N[m], prec.s[m]
         ps = p ** s
@@ -146,19 +150,27 @@ def frobenius_terms(X, basis, prec):
                 c = (Djm * Cja) % ps
                 if c == 0:
                     continue
-                gamma = tuple(p * (b + a + 1) for b, a in zip(beta, alpha))
+                gamma = tuple(p * (b + a + 1) - 1 + e for b, a, e in zip(beta, alpha, oneS))
                 U, J = tweak(gamma, d * n - n)
                 yield col, U, J, (c * scale) % q
 
 
 def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
-                 column_order=None, use_c=True, want_P=True, normalise=True):
+                 column_order=None, use_c=True, want_P=True, normalise=True, S=None):
     """Run the whole computation.  Returns a ZetaResult with
     basis, prec (r, N_m, M, q), Y (unnormalised b x b mod q), C (columns of
     p^{m-n-1} sigma mod p^r), F (= C diag(p^{n-m})), P (list a_0..a_b) and
-    the game log of the policy."""
+    the game log of the policy.
+
+    S: the index set of Prop. 3.3 (default {0..n}); f must be S-smooth and
+    d >= |S|.  Y depends on neither S nor the policy (module docstring)."""
+    S = full_S(n) if S is None else tuple(sorted(set(S)))
     if not is_smooth(n, d, p, coeffs):
         raise ValueError("f is not smooth")
+    if len(S) > d:
+        raise ValueError("Prop. 3.3 needs d >= |S|")
+    if S != full_S(n) and not is_S_smooth(n, d, p, coeffs, S):
+        raise ValueError("f is not S-smooth")
     X = Hypersurface(n, d, p, coeffs)
     basis = cohomology_basis(X)
     b = len(basis)
@@ -171,7 +183,7 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
 
     # Steps 3-4: terms combined by U into s x b blocks.
     blocks = {}
-    for col, U, J, c in frobenius_terms(X, basis, prec):
+    for col, U, J, c in frobenius_terms(X, basis, prec, S):
         if U not in blocks:
             blocks[U] = np.zeros((s, b), dtype=object)
         blk = blocks[U]
@@ -179,16 +191,15 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
     terms = list(blocks.items())
 
     # Step 5: the policy plays the game; chunks run Algorithm 2.
-    sec = Section(X, q, column_order=column_order)
+    sec = Section(X, q, column_order=column_order, S=S)
     parts_cache = {}
     log = GameLog()
-    one = (1,) * X.nv
-    S = set(range(X.nv))
+    oneS = tuple(1 if i in S else 0 for i in range(X.nv))
 
     def reduce_chunk(u, v, k, w):
         # invariant: x^u g / x^S is a polynomial, so g has no monomial mu with
-        # u_i + mu_i = 0; those rows must be zero.
-        zeros = tuple(i for i in range(X.nv) if u[i] == 0)
+        # u_i + mu_i = 0 for i in S; those rows must be zero.
+        zeros = tuple(i for i in S if u[i] == 0)
         if zeros:
             for row, mu in enumerate(Sidx.mons):
                 if any(mu[i] == 0 for i in zeros):
@@ -211,9 +222,9 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
     Y = np.zeros((b, b), dtype=object)
     H = [dict() for _ in range(b)]
     for u, w in final:
-        assert sum(u) == n
+        assert sum(u) == len(S) - 1
         for row, mu in enumerate(Sidx.mons):
-            e = sub_exp(add_exp(u, mu), one)
+            e = sub_exp(add_exp(u, mu), oneS)
             for col in range(b):
                 a = w[row, col]
                 if a:
@@ -225,6 +236,7 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
         res = ZetaResult()
         res.n, res.d, res.p, res.coeffs = n, d, p, list(coeffs)
         res.basis, res.prec, res.Y, res.log, res.policy = basis, prec, Y, log, policy
+        res.S = S
         return res
 
     # Step 7: normalisation.  Y = ((p s_m - 1)!/(n-1)!) p^{1-m} c, c known mod p^{r_m}.
@@ -253,6 +265,7 @@ def compute_zeta(n, d, p, coeffs, policy="depth_first", r=None, N=None,
     res.n, res.d, res.p, res.coeffs = n, d, p, list(coeffs)
     res.basis, res.prec, res.Y, res.C, res.F, res.log = basis, prec, Y, C, F, log
     res.policy = policy
+    res.S = S
     if want_P:
         res.P, res.eps = charpoly_lift(n, p, F, C, pole_orders, prec)
     return res

@@ -40,9 +40,11 @@ def test_berkowitz_companion_closed_form():
     assert algebra.berkowitz_charpoly(Cm) == coeffs
 
 
-def test_right_inverse_mod_prime_power():
+@pytest.mark.parametrize("k", [5, 30])
+def test_right_inverse_mod_prime_power(k):
+    # k = 5 runs the int64 elimination, k = 30 (q^2 > 2^62) the Python-integer one
     rng = random.Random(2)
-    p, k = 7, 5
+    p = 7
     q = p ** k
     for _ in range(5):
         M = [[rng.randrange(q) for _ in range(9)] for _ in range(5)]

@@ -139,8 +139,8 @@ def test_exact_divisibility_fails_for_a_planted_mistake(quartic_f11):
     (n, d, p, c), ref = quartic_f11
     orig = zeta.frobenius_terms
 
-    def broken(X, basis, prec):
-        for k, (col, U, J, val) in enumerate(orig(X, basis, prec)):
+    def broken(X, basis, prec, S=None):
+        for k, (col, U, J, val) in enumerate(orig(X, basis, prec, S)):
             yield col, U, J, (val * (1 if k % 7 else 2)) % prec.q
     zeta.frobenius_terms = broken
     try:
