@@ -105,6 +105,14 @@ typedef struct {
     /* ZETA_PATH_VECTOR: threads per block of the recurrence kernel (a
      * multiple of 32 in [64, 512]; 0 = the library's choice from s and b). */
     uint32_t block_threads;
+    /* The index set S of Prop. 3.3 as a bit mask over x_0..x_n (bit i set =
+     * i in S).  0 = automatic: S = {0..n} when d >= n + 1, else S = {n}.
+     * f must be S-smooth (Definition 3.1: d_i f for i in S and x_i d_i f
+     * for i not in S have no common zero; ZETA_ERR_NOT_SMOOTH otherwise)
+     * and |S| <= d (ZETA_ERR_UNSUPPORTED); bits above x_n: ZETA_ERR_ARG.
+     * P(T) does not depend on S.  ZETA_POLICY_COVER and
+     * ZETA_POLICY_LEARNED take S = {0..n} only (ZETA_ERR_UNSUPPORTED). */
+    uint32_t S_mask;
 } zeta_options;
 
 /* Stop after the unnormalised columns Y (no division by p^(v-m+1), no
@@ -350,8 +358,8 @@ zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options 
  * ------------------------------------------------------------------------- */
 typedef struct {
     uint32_t b, s, nv;          /* basis size, C(dn, n), n + 1 */
-    uint32_t sec_rows;          /* (n+1) * C(n(d-2)+n, n): rows (i, nu), i major */
-    uint32_t sec_cols;          /* C(kappa+n, n), kappa = (n+1)(d-2)+1 */
+    uint32_t sec_rows;          /* (n+1) * C(kappa-d+1+n, n): rows (i, nu), i major */
+    uint32_t sec_cols;          /* C(kappa+n, n), kappa = (n+1)(d-1)+1-|S| ((n+1)(d-2)+1 for S = {0..n}) */
     uint32_t h_rows;            /* C(dn-1, n): monomials of degree dn-n-1 */
     uint32_t r, M;
     uint64_t q;                 /* p^M */
@@ -363,15 +371,20 @@ typedef struct {
     uint64_t plan_merges;       /* move 2: duplicates combined */
     uint64_t plan_entries;      /* terms processed over all phases */
     uint64_t plan_cap;          /* largest number of merged terms waiting between two phases */
+    uint32_t kappa;             /* degree of the section's columns */
+    uint32_t S_mask;            /* the index set S used (bit i = i in S) */
 } zeta_plan_info;
 
 /* Host setup of one instance (Sec. 2.3-2.5, Prop. 2.1, Alg. 1, Prop. 3.3)
  * and the reduction game of opt->policy (Sec. 3.4, Sec. 4), statistics in info:
  *  sec:        sec_rows x sec_cols uint64 (row-major) -- the section of the
- *              Jacobian map M_kappa over Z/q: column gamma holds g_0..g_n with
- *              sum_i g_i d_i f = x^gamma (rows (i, nu), nu in Homog_{n(d-2)}).
- *  chain_U:    nchains x nv int32 -- start exponents U (Tweak of p(beta+alpha+1)),
- *              distinct, longest first.
+ *              map of J_S in degree kappa over Z/q: column gamma holds G_0..G_n
+ *              with sum_i G_i d_i f = x^gamma, G_i a multiple of x_i for i not
+ *              in S (rows (i, nu), nu in Homog_{kappa-d+1}; rows (i, nu) with
+ *              i not in S and nu_i = 0 are zero).  For S = {0..n}: the section
+ *              of M_kappa, nu in Homog_{n(d-2)}.
+ *  chain_U:    nchains x nv int32 -- start exponents U (Tweak of
+ *              p(beta+alpha+1) - 1 + 1_S), distinct, longest first.
  *  chain_terms:nchains x 2 uint32 -- [begin, end) ranges into the term arrays.
  *  term_rc:    nterms x 2 uint32 -- (row = index of J in Homog_{dn-n}, basis column).
  *  term_coeff: nterms uint64 -- (D_{j,m} C_{j,alpha} mod p^{s_m}) (p s_m - 1)!/(p(m+j) - 1)! mod q.
@@ -382,6 +395,20 @@ typedef struct {
 zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta_plan_info *info,
                       uint64_t *sec, int32_t *chain_U, uint32_t *chain_terms, uint32_t *term_rc,
                       uint64_t *term_coeff, uint64_t *fin);
+
+/* The index tables the device's step-matrix generation reads for one
+ * instance (host only).  The kernel forms, for output row r and input
+ * column j of Homog_{dn-n} (monomials omega_r, mu_j),
+ *   R_{u,v}[r, j] = sum_i (u_i + e_{r,i}) Sec[secrow[i s + r], rank_kappa(v + e_j - 1)]
+ * with e_j = monoS[j] = mu_j + 1 - 1_S, which is Prop. 3.3's
+ * x^S sum_i (u_i G_i / x_i + d_i G_i) on monomials for any S; and it adds
+ * the pole-order-n numerators at rank_{dn-n-1}(U + e_j - 1).
+ *  monoS:  s x nv int32 (the shifted exponents e_j).
+ *  secrow: nv x s int32, secrow[i s + r] = row (i, omega_r - 1_S + e_i) of
+ *          sec, or -1 where that exponent has a negative entry.
+ * Either buffer may be NULL. */
+zeta_status zeta_plan_tables(const zeta_hypersurface *hs, const zeta_options *opt, int32_t *monoS,
+                             int32_t *secrow);
 
 /* The moves of the plan the host scheduled for one instance (host only, no
  * device): the device executes exactly these.  Two calls: with NULL buffers

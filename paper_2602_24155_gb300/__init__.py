@@ -30,7 +30,8 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_charpoly", "zeta_batch", "zeta_batch_prepare", "zeta_batch_run", "zeta_batch_finish",
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
-           "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait", "zeta_plan_moves"]
+           "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait", "zeta_plan_moves",
+           "zeta_plan_tables"]
 FLAG_Y_ONLY = 1
 
 
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
     _fields_ = [("policy", ctypes.c_int), ("path", ctypes.c_int), ("r_override", ctypes.c_uint32),
                 ("N_override", ctypes.c_uint32 * 8), ("flags", ctypes.c_uint32),
                 ("policy_weights", ctypes.POINTER(ctypes.c_float)), ("policy_hidden", ctypes.c_uint32),
-                ("block_threads", ctypes.c_uint32)]
+                ("block_threads", ctypes.c_uint32), ("S_mask", ctypes.c_uint32)]
 
 
 TUNE_MAX = 8
@@ -87,7 +88,8 @@ class PlanInfo(ctypes.Structure):
                 ("nchains", ctypes.c_uint64), ("nterms", ctypes.c_uint64),
                 ("plan_chunks", ctypes.c_uint64), ("plan_steps", ctypes.c_uint64),
                 ("plan_column_steps", ctypes.c_uint64), ("plan_merges", ctypes.c_uint64),
-                ("plan_entries", ctypes.c_uint64), ("plan_cap", ctypes.c_uint64)]
+                ("plan_entries", ctypes.c_uint64), ("plan_cap", ctypes.c_uint64),
+                ("kappa", ctypes.c_uint32), ("S_mask", ctypes.c_uint32)]
 
 
 def _load():
@@ -135,6 +137,7 @@ def _load():
     lib.zeta_batch_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_size_t,
                                       P(Stats), P(Stats)]
     lib.zeta_batch_release.argtypes = [ctypes.c_void_p]
+    lib.zeta_plan_tables.argtypes = [P(Hypersurface), P(Options), ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_plan_moves.argtypes = [P(Hypersurface), P(Options), P(ctypes.c_size_t), P(ctypes.c_size_t),
                                     P(ctypes.c_size_t), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
@@ -161,9 +164,12 @@ LIB = _Lazy()
 
 
 def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0,
-             block_threads=0):
+             block_threads=0, S=None):
+    """S: the index set of Prop. 3.3 as variable indices (None = the library's choice: {0..n} when
+    d >= n + 1, else {n})."""
     o = Options()
     o.block_threads = block_threads
+    o.S_mask = sum(1 << int(i) for i in set(S)) if S else 0
     o.flags = FLAG_Y_ONLY if y_only else 0
     if weights is not None:
         w = np.ascontiguousarray(weights, dtype=np.float32)
@@ -377,6 +383,7 @@ def zeta_plan(spec, **opt):
     _check(None, LIB.zeta_plan(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(info), sec.ctypes.data,
                                U.ctypes.data, ct.ctypes.data, rc.ctypes.data, co.ctypes.data, fin.ctypes.data))
     return dict(b=info.b, s=info.s, nv=info.nv, r=info.r, M=info.M, q=info.q, h_rows=info.h_rows,
+                kappa=info.kappa, S=tuple(i for i in range(info.nv) if (info.S_mask >> i) & 1),
                 sec=sec, U=U, chain_terms=ct, term_rc=rc, term_coeff=co, fin=fin,
                 game=dict(chunks=info.plan_chunks, steps=info.plan_steps, column_steps=info.plan_column_steps,
                           merges=info.plan_merges, entries=info.plan_entries, cap=info.plan_cap))
@@ -481,6 +488,20 @@ def zeta_selftest_wait(ctx, limit_ms):
     w = ctypes.c_double(0.0)
     st = LIB.zeta_selftest_wait(ctx, limit_ms, ctypes.byref(w))
     return st, w.value
+
+
+def zeta_plan_tables(spec, **opt):
+    """The index tables the device's step-matrix generation reads (host only): dict with 'monoS'
+    (s x nv, exponents mu + 1 - 1_S) and 'secrow' (nv x s, rows of the section or -1)."""
+    hs = _hypersurface(spec)
+    o = _options(**opt)
+    info = PlanInfo()
+    _check(None, LIB.zeta_plan(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(info), None, None, None,
+                               None, None, None))
+    monoS = np.zeros((info.s, info.nv), dtype=np.int32)
+    secrow = np.zeros((info.nv, info.s), dtype=np.int32)
+    _check(None, LIB.zeta_plan_tables(ctypes.byref(hs), ctypes.byref(o), monoS.ctypes.data, secrow.ctypes.data))
+    return {"monoS": monoS, "secrow": secrow}
 
 
 def zeta_plan_moves(spec, **opt):

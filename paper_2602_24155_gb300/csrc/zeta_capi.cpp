@@ -432,6 +432,7 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
         info->sec_rows = X.sec_rows; info->sec_cols = X.sec_cols; info->h_rows = X.h_rows;
         info->r = X.r; info->M = X.M; info->q = X.q;
         info->nchains = X.chains.size(); info->nterms = X.terms.size();
+        info->kappa = X.kappa; info->S_mask = X.Smask;
     }
     if (sec) std::memcpy(sec, X.sec.data(), sizeof(uint64_t) * X.sec.size());
     for (size_t c = 0; c < X.chains.size(); c++) {
@@ -444,6 +445,18 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
         if (term_coeff) term_coeff[t] = X.terms[t].coeff;
     }
     if (fin) std::memcpy(fin, X.fin.data(), sizeof(uint64_t) * X.fin.size());
+    return ZETA_OK;
+}
+
+zeta_status zeta_plan_tables(const zeta_hypersurface *hs, const zeta_options *opt, int32_t *monoS,
+                             int32_t *secrow) {
+    if (!hs) return ZETA_ERR_ARG;
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    zeta_status st = prepare_instance(hs, &o, true, X);
+    if (st) return st;
+    if (monoS) std::memcpy(monoS, X.tab_monoS.data(), sizeof(int32_t) * X.tab_monoS.size());
+    if (secrow) std::memcpy(secrow, X.tab_secrow.data(), sizeof(int32_t) * X.tab_secrow.size());
     return ZETA_OK;
 }
 

@@ -3,7 +3,8 @@
 //   Sec. 2.3  monomial basis of H^n_dR(U) (cokernel of the Jacobian map)
 //   Sec. 2.4  Frobenius expansion (Prop. 2.1) -> start terms
 //   Sec. 2.5  precision r, N_m, M
-//   Sec. 3.1  Tweak (Algorithm 1); section of the Jacobian map used by R_{u,v}
+//   Sec. 3.1  Tweak (Algorithm 1); section of the map of J_S used by R_{u,v}
+//             (Prop. 3.3, for S = {0..n} or a smaller S with f S-smooth)
 //   Sec. 3.3  final Griffiths-Dwork reduction (step (2)) as a linear map
 //   Sec. 2.1  normalisation, P(T) = det(1 - T F), functional equation
 // All arithmetic mod p^M, M such that p^M < 2^63, in Montgomery form where it
@@ -268,6 +269,26 @@ static bool smooth(const Setup &S) {
     return (int)pivot_columns_mod_p((int)cols.size(), rows.count, A, S.p).size() == rows.count;
 }
 
+// Columns (i, nu) of the map of J_S (Definition 3.1) among those of jacobian_columns:
+// for i not in S only the multiples of x_i d_i f, i.e. nu_i >= 1.
+static bool in_JS(uint32_t Smask, int i, const int *nu) { return ((Smask >> i) & 1u) || nu[i] >= 1; }
+
+// S-smooth iff the map of J_S is onto Homog_kappa mod p, kappa = (n+1)(d-1)+1-|S|:
+// the n+1 generators of J_S (|S| of degree d-1, the others of degree d) have no
+// common zero iff they form a regular sequence, iff they span every form of the
+// degree one above the socle of their quotient (Macaulay).
+static bool s_smooth(const Setup &S, uint32_t Smask, int kappa) {
+    Monos rows, src;
+    std::vector<std::vector<std::pair<int, uint32_t>>> cols;
+    jacobian_columns(S, kappa, rows, src, cols);
+    std::vector<uint32_t> A((size_t)cols.size() * rows.count, 0);
+    for (size_t c = 0; c < cols.size(); c++) {
+        if (!in_JS(Smask, (int)(c / src.count), src.at((int)(c % src.count)))) continue;
+        for (auto &pr : cols[c]) A[c * rows.count + pr.first] = (A[c * rows.count + pr.first] + pr.second) % S.p;
+    }
+    return (int)pivot_columns_mod_p((int)cols.size(), rows.count, A, S.p).size() == rows.count;
+}
+
 // Basis of Sec. 2.3: non-pivot monomials of the image of M_k, k = dm - n - 1.
 static void cohomology_basis(const Setup &S, std::vector<uint32_t> &pole, std::vector<std::vector<int>> &exps) {
     for (int m = 1; m <= S.n; m++) {
@@ -376,8 +397,15 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     bool prime = p >= 2;
     for (uint32_t t = 2; t * t <= p && prime; t++) if (p % t == 0) prime = false;
     if (!prime || p < 7 || p >= 50 || d % p == 0 || p <= n) { X.error = "p must be a prime in [7, 50), p > n, p not dividing d"; return X.status = ZETA_ERR_UNSUPPORTED; }
-    if (d < n + 1) { X.error = "controlled reduction with S = {0..n} needs d >= n+1"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    // the index set S of Prop. 3.3: {0..n} when d >= n + 1, else {n}, unless the caller names one
+    const uint32_t full = (1u << (n + 1)) - 1;
+    const uint32_t Smask = (opt && opt->S_mask) ? opt->S_mask : (d >= n + 1 ? full : (1u << n));
+    if (Smask & ~full) { X.error = "S_mask names a variable beyond x_n"; return X.status = ZETA_ERR_ARG; }
+    const uint32_t Ssize = (uint32_t)__builtin_popcount(Smask);
+    if (Ssize > d) { X.error = "controlled reduction needs d >= |S| (Prop. 3.3)"; return X.status = ZETA_ERR_UNSUPPORTED; }
     X.n = n; X.d = d; X.p = p; X.nv = n + 1;
+    X.Smask = Smask;
+    X.base = Ssize - 1;
     Setup S;
     int ncoef = (int)binom(n + d, n);
     for (int t = 0; t < ncoef; t++)
@@ -385,6 +413,11 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     X.coeffs.assign(hs->coeffs, hs->coeffs + ncoef);
     setup_poly(S, hs);
     if (!smooth(S)) { X.error = "f is not smooth (Jacobian criterion)"; return X.status = ZETA_ERR_NOT_SMOOTH; }
+    X.kappa = (n + 1) * (d - 1) + 1 - Ssize;
+    if (Smask != full && !s_smooth(S, Smask, (int)X.kappa)) {
+        X.error = "f is not S-smooth (Definition 3.1)";
+        return X.status = ZETA_ERR_NOT_SMOOTH;
+    }
     cohomology_basis(S, X.pole, X.basis_exp);
     X.b = (uint32_t)X.pole.size();
     int64_t bexp = (binom(1, 0) * 0);
@@ -395,7 +428,6 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     }
     if ((int64_t)X.b != bexp) { X.error = "basis size disagrees with the Hodge count"; return X.status = ZETA_ERR_INTERNAL; }
     X.s = (uint32_t)binom(d * n - n + n, n);
-    X.kappa = (n + 1) * (d - 2) + 1;
     X.h_rows = (uint32_t)binom(d * n - n - 1 + n, n);
 
     // precision (Sec. 2.5): r_m, N_m, M
@@ -425,21 +457,45 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     Mont mq(q);
     const int nv = X.nv;
 
-    // Section: right inverse of M_kappa (Prop. 3.3 proof), Sec[(i,nu), gamma].
+    // Section: right inverse of the map of J_S in degree kappa (Prop. 3.3 proof),
+    // Sec[(i,nu), gamma] = coefficient of x^nu in G_i, sum_i G_i d_i f = x^gamma.
+    // Columns (i, nu) outside J_S stay zero, so Gauss-Jordan never pivots there
+    // and their rows of Sec are zero; for S = {0..n} every column is in.
     {
         Monos rows, src;
         std::vector<std::vector<std::pair<int, uint32_t>>> cols;
         jacobian_columns(S, X.kappa, rows, src, cols);
         int R = rows.count, C = (int)cols.size();
         std::vector<uint64_t> A((size_t)R * C, 0);
-        for (int c = 0; c < C; c++)
+        for (int c = 0; c < C; c++) {
+            if (!in_JS(Smask, c / src.count, src.at(c % src.count))) continue;
             for (auto &pr : cols[c]) A[(size_t)pr.first * C + c] = mq.add(A[(size_t)pr.first * C + c], mq.to(pr.second));
+        }
         std::vector<uint64_t> Xinv;
         if (!right_inverse(R, C, A, mq, p, Xinv)) { X.error = "section: Jacobian map not onto"; return X.status = ZETA_ERR_INTERNAL; }
         X.sec_rows = C;
         X.sec_cols = R;
         X.sec.resize((size_t)C * R);
         for (size_t t = 0; t < X.sec.size(); t++) X.sec[t] = mq.from(Xinv[t]);
+
+        // index tables of the device's step-matrix generation: with e = mu + 1 - 1_S the
+        // S = {0..n} formulas R[omega, mu] = sum_i (u_i + e_omega,i) Sec[(i, e_omega - 1 + e_i),
+        // v + e_mu - 1] and the numerator exponent U + e_mu - 1 are those of any S
+        Monos mS = monomials(nv, d * n - n);
+        X.tab_monoS.assign((size_t)mS.count * nv, 0);
+        X.tab_secrow.assign((size_t)nv * mS.count, -1);
+        std::vector<int> g(nv);
+        for (int r = 0; r < mS.count; r++) {
+            for (int z = 0; z < nv; z++) X.tab_monoS[(size_t)r * nv + z] = mS.at(r)[z] + 1 - (int)((Smask >> z) & 1u);
+            for (int i = 0; i < nv; i++) {
+                bool ok = true;
+                for (int z = 0; z < nv; z++) {
+                    g[z] = mS.at(r)[z] - (int)((Smask >> z) & 1u) + (z == i ? 1 : 0);
+                    if (g[z] < 0) ok = false;
+                }
+                if (ok) X.tab_secrow[(size_t)i * mS.count + r] = i * src.count + mono_rank(g.data(), nv, src.deg);
+            }
+        }
     }
 
     // Final reduction map (Sec. 3.3 step (2)): Fin[beta, h], h in Homog_{dn-n-1}.
@@ -567,7 +623,9 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
                         if (!c) continue;
                         uint64_t coeff = mulmod_slow(c, scale, q);
                         if (!coeff) continue;
-                        for (int z = 0; z < nv; z++) gamma[z] = (int)p * (beta[z] + mj[j].at(a)[z] + 1);
+                        // x^{p(beta+alpha+1)-1} over x^S: gamma = p(beta+alpha+1) - 1 + 1_S
+                        for (int z = 0; z < nv; z++)
+                            gamma[z] = (int)p * (beta[z] + mj[j].at(a)[z] + 1) - 1 + (int)((Smask >> z) & 1u);
                         // Tweak(gamma, dn - n): remove units from the front
                         int left = (int)(d * n - n);
                         for (int z = 0; z < nv; z++) {
@@ -607,7 +665,7 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
             ch.term_begin = (uint32_t)X.terms.size();
             X.terms.insert(X.terms.end(), chain_terms[ci].begin(), chain_terms[ci].end());
             ch.term_end = (uint32_t)X.terms.size();
-            uint64_t steps = (uint64_t)(normU(ci) - (int)n) / d;
+            uint64_t steps = (uint64_t)(normU(ci) - (int)X.base) / d;
             ch.work = steps * X.b * (uint64_t)X.s * X.s;
             X.chains.push_back(ch);
         }

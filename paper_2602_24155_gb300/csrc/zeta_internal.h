@@ -73,7 +73,9 @@ struct Instance {
     std::vector<uint32_t> coeffs;
     // sizes
     uint32_t b = 0, s = 0;       // basis size, |Homog_{dn-n}|
-    uint32_t kappa = 0;          // (n+1)(d-2)+1
+    uint32_t kappa = 0;          // (n+1)(d-1)+1-|S|; (n+1)(d-2)+1 for S = {0..n}
+    uint32_t Smask = 0;          // index set S of Prop. 3.3 (bit i = i in S)
+    uint32_t base = 0;           // |S| - 1: |u| of a term at pole order n
     uint32_t sec_rows = 0, sec_cols = 0;
     uint32_t h_rows = 0;         // |Homog_{dn-n-1}|
     // precision
@@ -88,6 +90,9 @@ struct Instance {
     std::vector<Chain> chains;
     std::vector<Term> terms;
     std::vector<uint64_t> fin;   // b x h_rows final reduction map mod q
+    // index tables of the device's step-matrix generation (zeta_plan_tables)
+    std::vector<int32_t> tab_monoS;   // s x nv: mu + 1 - 1_S
+    std::vector<int32_t> tab_secrow;  // nv x s: row (i, omega - 1_S + e_i) of sec, or -1
     Plan plan;
     PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
     // per level t: exponent -> terms reaching it in the p-chunk game with Algorithm 3

@@ -799,38 +799,6 @@ static zeta_status upload(DeviceEngine *e, const char *name, const std::vector<T
     return ZETA_OK;
 }
 
-static int host_rank(const int *ex, int nv, int deg) {
-    long long idx = 0;
-    int rem = deg;
-    for (int i = 0; i < nv - 1; i++) {
-        int k = nv - i - 1;
-        int top = rem - ex[i] - 1;
-        if (top >= 0) {
-            long long r = 1;
-            for (int t = 1; t <= k; t++) r = r * (top + t) / t;
-            idx += r;
-        }
-        rem -= ex[i];
-    }
-    return (int)idx;
-}
-
-static void host_monos(int nv, int deg, std::vector<int> &out) {
-    std::vector<int> cur(nv, 0);
-    std::function<void(int, int)> rec = [&](int pos, int rem) {
-        if (pos == nv - 1) {
-            cur[pos] = rem;
-            out.insert(out.end(), cur.begin(), cur.end());
-            return;
-        }
-        for (int t = rem; t >= 0; t--) {
-            cur[pos] = t;
-            rec(pos + 1, rem - t);
-        }
-    };
-    if (deg >= 0) rec(0, deg);
-}
-
 struct DeviceBatch {
     cudaStream_t stream = nullptr;  // the lane every upload, launch and download of this batch uses
     std::vector<Instance *> insts;
@@ -921,7 +889,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     B->policy = policy;
     B->path = path;
 
-    std::map<std::pair<int, int>, uint32_t> tab_of;
+    std::map<uint64_t, uint32_t> tab_of;  // (n, d, S) -> table set
     std::vector<DTab> tabs;
     std::vector<int32_t> tabpool;
     std::vector<DInst> dinst;
@@ -936,32 +904,20 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     size_t max_block_words = 0;
     for (size_t ii = 0; ii < batch.size(); ii++) {
         Instance *X = batch[ii];
-        auto key = std::make_pair((int)X->n, (int)X->d);
+        const uint64_t key = ((uint64_t)X->n << 48) | ((uint64_t)X->d << 32) | X->Smask;
         if (!tab_of.count(key)) {
+            // index tables built by the host setup (they depend on n, d and S only):
+            // monoS = mu + 1 - 1_S, secrow[i][omega] = row (i, omega - 1_S + e_i) of Sec or -1.
+            // The kernel reads them with the formulas of S = {0..n}; with the section of J_S
+            // and the shifted exponents those are Prop. 3.3 for the instance's S.
             DTab T;
             T.nv = X->nv;
             T.s = X->s;
             T.h_rows = X->h_rows;
-            std::vector<int> mS;
-            host_monos(X->nv, X->d * X->n - X->n, mS);
             T.monoS_off = (uint32_t)tabpool.size();
-            tabpool.insert(tabpool.end(), mS.begin(), mS.end());
-            // secrow[i][omega] = row (i, omega - 1 + e_i) of Sec, -1 if a coordinate is negative
-            int srcdeg = X->n * (X->d - 2);
-            std::vector<int> tmp;
-            host_monos(X->nv, srcdeg, tmp);
-            int nsrc = (int)tmp.size() / X->nv;
+            tabpool.insert(tabpool.end(), X->tab_monoS.begin(), X->tab_monoS.end());
             T.secrow_off = (uint32_t)tabpool.size();
-            for (uint32_t i = 0; i < X->nv; i++)
-                for (uint32_t r = 0; r < X->s; r++) {
-                    int g[kMaxVars];
-                    bool ok = true;
-                    for (uint32_t t = 0; t < X->nv; t++) {
-                        g[t] = mS[r * X->nv + t] - 1 + (t == i ? 1 : 0);
-                        if (g[t] < 0) ok = false;
-                    }
-                    tabpool.push_back(ok ? (int32_t)(i * nsrc + host_rank(g, X->nv, srcdeg)) : -1);
-                }
+            tabpool.insert(tabpool.end(), X->tab_secrow.begin(), X->tab_secrow.end());
             tab_of[key] = (uint32_t)tabs.size();
             tabs.push_back(T);
         }

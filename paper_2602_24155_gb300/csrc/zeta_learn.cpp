@@ -249,6 +249,7 @@ zeta_status reference_contributions(Instance &X) {
 zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<uint32_t> &group_off,
                            std::vector<uint32_t> &labels, std::vector<int32_t> &costs) {
     if (X.nv > 4) { X.error = "the policy features cover at most four variables"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    if (X.Smask != (1u << X.nv) - 1) { X.error = "the learned policy takes S = {0..n} only"; return X.status = ZETA_ERR_UNSUPPORTED; }
     zeta_status st = reference_contributions(X);  // what the network sees of U
     if (st) return st;
     X.teacher = true;

@@ -4,7 +4,8 @@
 // the chunks (v, k) of move 1 and the merge destination of move 2.
 //
 //  depth-first  (Sec. 4.2): each start term alone, greedy v (Algorithm 3),
-//               largest k with v in V_full(u, k) and |u - k v| >= n; never merges.
+//               largest k with v in V_full(u, k) and |u - k v| >= |S| - 1;
+//               never merges.
 //  p-chunk      (Sec. 4.1): all terms of the largest pole order K = p t are
 //               reduced by p (by p - n when K = p), then terms with equal u
 //               are combined; the start terms of pole order p(t-1) join.
@@ -39,13 +40,13 @@ namespace zeta {
 
 namespace {
 
-// Algorithm 3 with S = {0..n}: S scanned in ascending order, the count tested
-// before every increment of the round-robin loop.
-void greedy_v(const int32_t *U, int nv, int d, int *v) {
+// Algorithm 3: S scanned in ascending order (Smask, bit t = t in S), the count
+// tested before every increment of the round-robin loop.
+void greedy_v(const int32_t *U, int nv, int d, int *v, uint32_t Smask) {
     int i = d;
     for (int t = 0; t < nv; t++) v[t] = 0;
     for (int t = 0; t < nv && i > 0; t++)
-        if (U[t] != 0) { v[t] = 1; i--; }
+        if (((Smask >> t) & 1u) && U[t] != 0) { v[t] = 1; i--; }
     while (i > 0)
         for (int t = 0; t < nv && i > 0; t++)
             if (v[t] < U[t]) { v[t]++; i--; }
@@ -57,9 +58,9 @@ int norm(const int32_t *U, int nv) {
     return s;
 }
 
-// largest k with U - k v >= 0 and |U - k v| >= n
-int k_max(const int32_t *U, const int *v, int nv, int n, int d) {
-    int k = (norm(U, nv) - n) / d;
+// largest k with U - k v >= 0 and |U - k v| >= base (= |S| - 1, the norm at pole order n)
+int k_max(const int32_t *U, const int *v, int nv, int base, int d) {
+    int k = (norm(U, nv) - base) / d;
     for (int t = 0; t < nv; t++)
         if (v[t] > 0) k = std::min(k, U[t] / v[t]);
     return k;
@@ -77,12 +78,12 @@ uint64_t pack(const int32_t *U, int nv) {
 template <typename Stop>
 void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_steps,
                  const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
-    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
+    const int nv = (int)X.nv, base = (int)X.base, d = (int)X.d;
     int left = max_steps;
-    while (norm(U, nv) > n && left > 0 && !stop(U)) {
+    while (norm(U, nv) > base && left > 0 && !stop(U)) {
         int v[kMaxVars];
-        if (!(choose && choose(U, left, v))) greedy_v(U, nv, d, v);
-        int k = std::min(k_max(U, v, nv, n, d), left);
+        if (!(choose && choose(U, left, v))) greedy_v(U, nv, d, v, X.Smask);
+        int k = std::min(k_max(U, v, nv, base, d), left);
         if (k <= 0) break;
         PlanChunk c;
         std::memset(&c, 0, sizeof(c));
@@ -199,10 +200,10 @@ std::vector<std::vector<int32_t>> cover_destinations(
             std::array<int32_t, kMaxVars> u{};
             for (int t = 0; t < nv; t++) u[t] = P.entries[e0 + i].U[t];
             int leftsteps = L;
-            while (leftsteps > 0 && norm(u.data(), nv) > (int)X.n) {
+            while (leftsteps > 0 && norm(u.data(), nv) > (int)X.base) {
                 int v[kMaxVars];  // the direction the level will play (the same chooser as play_chunks)
-                if (!(choose && choose(u.data(), leftsteps, v))) greedy_v(u.data(), nv, d, v);
-                const int k = std::min(k_max(u.data(), v, nv, (int)X.n, d), leftsteps);
+                if (!(choose && choose(u.data(), leftsteps, v))) greedy_v(u.data(), nv, d, v, X.Smask);
+                const int k = std::min(k_max(u.data(), v, nv, (int)X.base, d), leftsteps);
                 if (k <= 0) break;
                 for (int t = 0; t < nv; t++) u[t] -= k * v[t];
                 leftsteps -= k;
@@ -294,8 +295,13 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     Plan &P = X.plan;
     P = Plan();
     if (X.b > 32) { X.error = "more than 32 basis columns"; return X.status = ZETA_ERR_UNSUPPORTED; }
-    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p;
-    auto pole = [&](const int32_t *U) { return (norm(U, nv) - n) / d + n; };
+    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p, base = (int)X.base;
+    if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_COVER || policy == ZETA_POLICY_LEARNED || X.teacher)) {
+        X.error = "the cover and learned policies take S = {0..n} only";
+        return X.status = ZETA_ERR_UNSUPPORTED;
+    }
+    // a term of pole order K has |u| = |S| - 1 + d (K - n)
+    auto pole = [&](const int32_t *U) { return (norm(U, nv) - base) / d + n; };
     auto new_entry = [&](const int32_t *U) {
         PlanEntry e;
         std::memset(&e, 0, sizeof(e));
@@ -372,7 +378,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
             if (cover_next && !dest_of[ei - e0].empty()) path_chunks(X, U, dest_of[ei - e0].data(), cover_L, e.live);
             else play_chunks(X, U, e.live, stop_for, max_steps(e), choose);
             e.chunk_end = (uint32_t)P.chunks.size();
-            if (norm(U, nv) == n) {
+            if (norm(U, nv) == base) {
                 e.dest = -1;
                 continue;
             }
@@ -446,13 +452,13 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     return validate_plan(X);
 }
 
-// Every chunk of the plan is a legal move of the game (Prop. 3.3 with
-// S = {0..n}: |v| = d, v <= u, u_i != 0 => v_i != 0, k >= 1, pole order >= n
-// after the chunk) and every entry ends where its routing says: at the
-// exponent of its destination block, or at pole order n.
+// Every chunk of the plan is a legal move of the game (Prop. 3.3: |v| = d,
+// v <= u, u_i != 0 => v_i != 0 for i in S, k >= 1, pole order >= n after the
+// chunk, i.e. |u| >= |S| - 1) and every entry ends where its routing says: at
+// the exponent of its destination block, or at pole order n.
 zeta_status validate_plan(Instance &X) {
     const Plan &P = X.plan;
-    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
+    const int nv = (int)X.nv, base = (int)X.base, d = (int)X.d;
     for (size_t ph = 0; ph + 1 < P.phase_begin.size(); ph++) {
         std::unordered_map<int32_t, std::vector<int32_t>> dest_U;
         for (uint32_t ei = P.phase_begin[ph]; ei < P.phase_begin[ph + 1]; ei++) {
@@ -465,20 +471,21 @@ zeta_status validate_plan(Instance &X) {
                 bool ok = c.k >= 1;
                 for (int t = 0; t < nv; t++) {
                     sv += c.v[t];
-                    if (c.v[t] < 0 || U[t] - c.k * c.v[t] < 0 || (U[t] != 0 && c.v[t] == 0)) ok = false;
+                    if (c.v[t] < 0 || U[t] - c.k * c.v[t] < 0 || (((X.Smask >> t) & 1u) && U[t] != 0 && c.v[t] == 0))
+                        ok = false;
                 }
                 if (!ok || sv != d) {
                     X.error = "plan has an illegal chunk";
                     return X.status = ZETA_ERR_INTERNAL;
                 }
                 for (int t = 0; t < nv; t++) U[t] -= c.k * c.v[t];
-                if (norm(U, nv) < n) {
+                if (norm(U, nv) < base) {
                     X.error = "plan goes below pole order n";
                     return X.status = ZETA_ERR_INTERNAL;
                 }
             }
             if (e.dest < 0) {
-                if (norm(U, nv) != n) {
+                if (norm(U, nv) != base) {
                     X.error = "plan leaves a term above pole order n";
                     return X.status = ZETA_ERR_INTERNAL;
                 }

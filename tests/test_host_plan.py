@@ -179,17 +179,53 @@ def _step_matrices(spec, plan, U, v, k):
     return A, B, x
 
 
-def replay_moves(spec, plan, moves):
+def _step_matrices_from_tables(spec, plan, tables, U, v, k):
+    """A and B as the device forms them from the exported index tables (zeta_plan_tables): with e_j = monoS[j],
+    column j reads Sec column rank_kappa(v + e_j - 1), row r reads Sec rows secrow[i][r], weights v_i (A) and
+    x_i + e_{r,i} (B).  No knowledge of S is used here: it is all in the tables and the section."""
+    n, d, p, coeffs = spec
+    nv = n + 1
+    q = int(plan["q"])
+    e = [tuple(int(a) for a in row) for row in tables["monoS"]]
+    secrow = tables["secrow"]
+    s = len(e)
+    kap = _rank_table(nv, int(plan["kappa"]))
+    sec = plan["sec"]
+    x = tuple(a - k * bb for a, bb in zip(U, v))
+    A = np.zeros((s, s), dtype=object)
+    B = np.zeros((s, s), dtype=object)
+    for j in range(s):
+        g = tuple(v[t] + e[j][t] - 1 for t in range(nv))
+        if min(g) < 0:
+            continue
+        col = kap[g]
+        for r in range(s):
+            a = bb = 0
+            for i in range(nv):
+                row = int(secrow[i][r])
+                if row < 0:
+                    continue
+                val = int(sec[row, col])
+                a += v[i] * val
+                bb += (x[i] + e[r][i]) * val
+            A[r, j] = a % q
+            B[r, j] = bb % q
+    return A, B, x
+
+
+def replay_moves(spec, plan, moves, tables=None):
     """The device executor's semantics in plain Python: phase by phase, every entry starts from its arrival block
     and/or its start chain, plays its chunks (Algorithm 2), then is stored or added into its destination block of
-    the next phase, or accumulated into the numerators at pole order n."""
+    the next phase, or accumulated into the numerators at pole order n.  With `tables` the step matrices and the
+    numerator exponents come from the device's index tables (any S); without, from the S = {0..n} formula."""
     n, d, p, coeffs = spec
     nv = n + 1
     q = int(plan["q"])
     b = plan["b"]
-    mS = monomials(nv, d * n - n)
+    mS = monomials(nv, d * n - n) if tables is None else [tuple(int(a) for a in r) for r in tables["monoS"]]
     s = len(mS)
     hpos = _rank_table(nv, d * n - n - 1)
+    base = n if tables is None else len(plan["S"]) - 1
     H = np.zeros((len(hpos), b), dtype=object)
     ph, ent, chk = moves["phase_begin"], moves["entries"], moves["chunks"]
     cur = {}
@@ -211,13 +247,14 @@ def replay_moves(spec, plan, moves):
                 k = int(chk[ci][nv])
                 key = (U, v, k)
                 if key not in cache:
-                    cache[key] = _step_matrices(spec, plan, U, v, k)
+                    cache[key] = (_step_matrices(spec, plan, U, v, k) if tables is None
+                                  else _step_matrices_from_tables(spec, plan, tables, U, v, k))
                 A, B, x = cache[key]
                 W = ozeta.horner_python(A, B, W, k, q)
                 U = x
             assert all((live >> c) & 1 or not W[:, c].any() for c in range(b))
             if dest < 0:
-                assert sum(U) == n
+                assert sum(U) == base
                 for j, mu in enumerate(mS):
                     g = tuple(U[t] + mu[t] - 1 for t in range(nv))
                     if min(g) < 0:
@@ -281,3 +318,79 @@ def test_moduli_above_2_60_are_rejected():
     with pytest.raises(z.ZetaError) as err:
         z.zeta_query((n, d, p, c), r=6)
     assert err.value.status == 4
+
+
+# ---------------------------------------------------------------------------
+# General S (Prop. 3.3 with S other than {0..n}): the same device tables and kernel formula
+# ---------------------------------------------------------------------------
+def _cubic_surface(p, seed=7):
+    att = 0
+    while True:
+        c = zi.dense_candidate(3, 3, p, seed, p, att)
+        att += 1
+        if cohomology.is_smooth(3, 3, p, c) and cohomology.is_S_smooth(3, 3, p, c, (3,)):
+            return (3, 3, p, c)
+
+
+@pytest.mark.parametrize("which", [("quartic_curve_f11", 0), ("quintic_curves", 3)])
+def test_device_tables_for_S_all_are_the_monomial_formula(which):
+    n, d, p, c, _ = zi.draw_instance(*which, cohomology.is_smooth)
+    nv = n + 1
+    tab = z.zeta_plan_tables((n, d, p, c))
+    mS = monomials(nv, d * n - n)
+    assert [tuple(r) for r in tab["monoS"]] == mS
+    src = _rank_table(nv, n * (d - 2))
+    for i in range(nv):
+        for r, om in enumerate(mS):
+            nu = tuple(om[t] - 1 + (1 if t == i else 0) for t in range(nv))
+            assert tab["secrow"][i][r] == (-1 if min(nu) < 0 else i * len(src) + src[nu])
+
+
+@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var"])
+def test_general_S_replay_on_a_curve_matches_oracle(policy):
+    """The quartic over F_11 with S = {1, 2}: the library's section of J_S, start terms, tables and moves, replayed
+    through the device formula, give the oracle's Y (which does not depend on S) and P(T)."""
+    n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
+    spec = (n, d, p, c)
+    opt = {"policy": policy, "S": (1, 2)}
+    plan = z.zeta_plan(spec, **opt)
+    assert plan["S"] == (1, 2) and plan["kappa"] == 3 * 3 + 1 - 2
+    H = replay_moves(spec, plan, z.zeta_plan_moves(spec, **opt), z.zeta_plan_tables(spec, **opt))
+    F, Y, P = z.zeta_finish(spec, H, **opt)
+    res = ozeta.compute_zeta(n, d, p, c)
+    assert (Y.astype(object) == res.Y).all()
+    assert P == res.P
+
+
+@pytest.mark.parametrize("p,policy", [(7, "depth_first"), (7, "p_chunk"), (7, "var_by_var"), (11, "p_chunk")])
+def test_general_S_replay_on_cubic_surfaces_matches_oracle(p, policy):
+    """Cubic surfaces (d = 3 < n + 1): the library picks S = {3}; its game counts equal the oracle's (separate
+    code), and the replayed device formula gives the oracle's Y and P(T)."""
+    spec = _cubic_surface(p)
+    plan = z.zeta_plan(spec, policy=policy)
+    assert plan["S"] == (3,)
+    res = ozeta.compute_zeta(*spec, policy=policy, S=(3,))
+    g = plan["game"]
+    assert (g["chunks"], g["steps"], g["merges"]) == (res.log.chunks, res.log.steps, res.log.merges)
+    H = replay_moves(spec, plan, z.zeta_plan_moves(spec, policy=policy), z.zeta_plan_tables(spec, policy=policy))
+    F, Y, P = z.zeta_finish(spec, H)
+    assert (Y.astype(object) == res.Y).all()
+    assert P == res.P
+
+
+def test_general_S_refusals():
+    n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((n, d, p, c), S=(2,))            # not {2}-smooth (oracle: is_S_smooth is False)
+    assert e.value.status == 2 and not cohomology.is_S_smooth(n, d, p, c, (2,))
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((n, d, p, c), S=(3,))            # x_3 does not exist in P^2
+    assert e.value.status == 1
+    for policy in ("cover", "learned"):
+        with pytest.raises(z.ZetaError) as e:
+            z.zeta_plan((n, d, p, c), policy=policy, S=(1, 2))
+        assert e.value.status == 3
+    spec = _cubic_surface(7)
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query(spec, S=(0, 1, 2, 3))            # |S| = 4 > d = 3
+    assert e.value.status == 3
