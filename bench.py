@@ -48,7 +48,9 @@ def _peaks():
 
 
 def _instances(rank, count):
-    """Instances rank*count .. rank*count+count-1 of the quintic-curve workload."""
+    """Instances rank*count .. rank*count+count-1 of the quintic-curve workload, filtered by the oracle's
+    smoothness test: for the reference arm (the oracle) and the multi-process tests only; the timed path draws
+    the same instances through the library (_instances_lib)."""
     from oracle.cohomology import is_smooth  # the oracle's smoothness predicate only filters
     out = []
     for i in range(rank * count, rank * count + count):
@@ -211,6 +213,40 @@ def _k3_survey(z, ctx, stream, torch):
             "column_steps": tot["column_steps"], "heights": dict(sorted(hist.items()))}
 
 
+def _cubic_survey(z, ctx, stream, torch):
+    """1024 dense cubic surfaces over F_7, F_11, F_13 at full precision in one persistent launch: d = 3 < n + 1, so
+    the reduction runs with S = {3} (Prop. 3.3 for a smaller index set; same kernel, section of J_S).  Parity with
+    the oracle, point counts and the Gauss-sum closed form is in tests/test_gpu_general_s.py."""
+
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c))       # smooth and {3}-smooth
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    count = zi.WORKLOADS["cubic_surfaces"]["count"]
+    specs = [zi.draw_instance("cubic_surfaces", i, accept)[:4] for i in range(count)]
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk")
+    plan.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    P, per, tot = plan.finish()
+    plan.release()
+    ms = e0.elapsed_time(e1)
+    ok = sum(1 for x in per if x["status"] == 0)
+    return {"workload": "cubic_surfaces_%d" % count, "primes": [7, 11, 13], "S": [3], "s": 84, "b": 6,
+            "policy": "p_chunk", "ms_per_launch": ms, "zeta_per_s": count / (ms / 1000.0), "launches": 1,
+            "column_steps": tot["column_steps"], "completed": "%d/%d" % (ok, count),
+            "ms_host_setup": tot["ms_host_setup"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +262,8 @@ def main():
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k3", action="store_true", help="skip the K3 height survey (512 surfaces, precision 1)")
+    ap.add_argument("--no-cubic", action="store_true",
+                    help="skip the cubic-surface line (1024 surfaces, S = {3}, full precision)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -402,6 +440,11 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_k3:
         line["k3_heights"] = _k3_survey(z, ctx, stream, torch)
+    if rank == 0 and world == 1 and not args.no_cubic:
+        try:
+            line["cubic_surfaces"] = _cubic_survey(z, ctx, stream, torch)
+        except Exception as exc:   # reported, never a reason to lose the main line
+            line["cubic_surfaces"] = {"error": repr(exc)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample_n = max(1, min(cores, 16))

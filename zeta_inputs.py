@@ -114,6 +114,8 @@ WORKLOADS = {
     "quartic_k3": dict(n=3, d=4, count=512, seed=2),
     # dense quintic surfaces in P^3 over F_7
     "quintic_surfaces": dict(n=3, d=5, count=256, seed=3),
+    # dense cubic surfaces in P^3 over F_7, F_11, F_13 (d < n + 1: reduction with S = {3})
+    "cubic_surfaces": dict(n=3, d=3, count=1024, seed=4),
 }
 
 
@@ -128,6 +130,8 @@ def instance_shape(workload, i):
         return 3, 4, PRIMES_K3[i % 3], (i % 10) == 9
     if workload == "quintic_surfaces":
         return 3, 5, 7, False
+    if workload == "cubic_surfaces":
+        return 3, 3, PRIMES_K3[i % 3], False
     raise KeyError(workload)
 
 
