@@ -27,10 +27,12 @@
  *    the row echelon form over F_p of the image of the Jacobian map M_k
  *    (columns in the order above).  Basis order: m ascending, then monomial
  *    order.  b = dim = ((d-1)^{n+1} + (-1)^{n+1}(d-1)) / d.
- *  - Supported: S = {0..n} controlled reduction (Prop. 3.3), which needs
- *    d >= n+1; p^M < 2^60 (the device keeps residues as two 30-bit limbs, or
- *    as at most eight balanced base-256 digits on the tensor cores).  Other
- *    inputs return ZETA_ERR_UNSUPPORTED or ZETA_ERR_PRECISION.
+ *  - Supported: controlled reduction (Prop. 3.3) with S = {0..n} when
+ *    d >= n+1 and S = {n} otherwise (zeta_options.S_mask chooses another
+ *    S); step matrices of side s = C(dn, n) <= 512; p^M < 2^60 (the device
+ *    keeps residues as two 30-bit limbs, or as at most eight balanced
+ *    base-256 digits on the tensor cores).  Other inputs return
+ *    ZETA_ERR_UNSUPPORTED or ZETA_ERR_PRECISION.
  *  - Calls are synchronous: they return after the device work has finished.
  *    One context must not be used from two host threads at once.
  */

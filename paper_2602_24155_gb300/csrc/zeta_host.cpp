@@ -403,6 +403,9 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     if (Smask & ~full) { X.error = "S_mask names a variable beyond x_n"; return X.status = ZETA_ERR_ARG; }
     const uint32_t Ssize = (uint32_t)__builtin_popcount(Smask);
     if (Ssize > d) { X.error = "controlled reduction needs d >= |S| (Prop. 3.3)"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    // the executor holds step matrices of side s = C(dn, n) <= 512 (cubic fourfolds: s = 3003); refused
+    // before the smoothness tests, whose eliminations grow with s
+    if (binom(d * n, n) > 512) { X.error = "step matrices larger than 512 x 512 (C(dn, n) > 512)"; return X.status = ZETA_ERR_UNSUPPORTED; }
     X.n = n; X.d = d; X.p = p; X.nv = n + 1;
     X.Smask = Smask;
     X.base = Ssize - 1;

@@ -394,3 +394,26 @@ def test_general_S_refusals():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_query(spec, S=(0, 1, 2, 3))            # |S| = 4 > d = 3
     assert e.value.status == 3
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_query((5, 3, 7, zi.fermat(5, 3)))      # cubic fourfold: s = C(15, 5) = 3003 > 512
+    assert e.value.status == 3
+
+
+def test_cubic_threefold_is_planned_with_S_n():
+    """A cubic threefold over F_11 (n = 4, d = 3, s = 495): S = {4}, kappa = 10, and the precision rules give
+    r = 6, M = 16; the host plans it (a legal plan, checked move by move), the device is not run here."""
+    n, d, p = 4, 3, 11
+    att = 0
+    while True:
+        c = zi.dense_candidate(n, d, p, 11, 0, att)
+        att += 1
+        try:
+            b, r, M, s = z.zeta_query((n, d, p, c))
+            break
+        except z.ZetaError as e:
+            assert e.status == 2
+    assert (b, r, M, s) == (10, 6, 16, 495)
+    assert cohomology.is_S_smooth(n, d, p, c, (4,))          # the oracle's test accepts the same instance
+    plan = z.zeta_plan((n, d, p, c), policy="p_chunk")
+    assert plan["S"] == (4,) and plan["kappa"] == 10
+    assert plan["game"]["column_steps"] > 0
