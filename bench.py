@@ -241,10 +241,15 @@ def _cubic_survey(z, ctx, stream, torch):
     plan.release()
     ms = e0.elapsed_time(e1)
     ok = sum(1 for x in per if x["status"] == 0)
-    return {"workload": "cubic_surfaces_%d" % count, "primes": [7, 11, 13], "S": [3], "s": 84, "b": 6,
+    s = 84
+    achieved = tot["column_steps"] * s * s / (ms / 1000.0) / 1e12
+    alu_peak = 152 * 64 / 6 * 2070.0 * 1e6 / 1e12      # the main line's ALU peak at the maximum SM clock
+    return {"workload": "cubic_surfaces_%d" % count, "primes": [7, 11, 13], "S": [3], "s": s, "b": 6,
             "policy": "p_chunk", "ms_per_launch": ms, "zeta_per_s": count / (ms / 1000.0), "launches": 1,
             "column_steps": tot["column_steps"], "completed": "%d/%d" % (ok, count),
-            "ms_host_setup": tot["ms_host_setup"]}
+            "ms_host_setup": tot["ms_host_setup"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
+                         "frac": achieved / alu_peak}}
 
 
 def main():
