@@ -112,8 +112,8 @@ typedef struct {
      * f must be S-smooth (Definition 3.1: d_i f for i in S and x_i d_i f
      * for i not in S have no common zero; ZETA_ERR_NOT_SMOOTH otherwise)
      * and |S| <= d (ZETA_ERR_UNSUPPORTED); bits above x_n: ZETA_ERR_ARG.
-     * P(T) does not depend on S.  ZETA_POLICY_COVER and
-     * ZETA_POLICY_LEARNED take S = {0..n} only (ZETA_ERR_UNSUPPORTED). */
+     * P(T) does not depend on S.  ZETA_POLICY_LEARNED takes S = {0..n}
+     * only (ZETA_ERR_UNSUPPORTED). */
     uint32_t S_mask;
 } zeta_options;
 

@@ -16,12 +16,12 @@
 //               chunks until u_t = 0 (or pole order n), then combines.
 //  cover        (this library, a search over move 2 of the game): the levels
 //               of p-chunk, but every term of a level chooses its destination
-//               so that terms land together.  With S = {0..n} every step
-//               lowers each nonzero coordinate by at least 1, so after L
-//               steps a term with all U_i >= L can reach exactly the V with
-//               0 <= V <= U - L 1 and |V| = |U| - d L; a group of terms can
+//               so that terms land together.  Every step lowers each nonzero
+//               coordinate in S by at least 1, so after L steps a term with
+//               U_i >= L for i in S can reach exactly the V with
+//               0 <= V <= U - L 1_S and |V| = |U| - d L; a group of terms can
 //               share a destination iff the positive part of the
-//               componentwise minimum of their boxes U - L 1 still sums to
+//               componentwise minimum of their boxes U - L 1_S still sums to
 //               |V|.  Terms first join the next level's start terms they
 //               dominate, then groups grow greedily on the compatibility graph
 //               (seeds in decreasing degree, members keeping the most mass of
@@ -99,16 +99,19 @@ void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_step
     }
 }
 
-// Chunks of a path of L steps from U to V = U - L 1 - E (E >= 0, |E| = (d - nv) L,
-// every U_i >= L): step j lowers every coordinate by 1 and takes d - nv extra
-// units from the list of E's units sorted by coordinate; equal consecutive
-// steps form one chunk.  Every step is legal: all coordinates stay >= 1 until
-// the last step (S = {0..n} is covered) and the pole order stays >= n.
+// Chunks of a path of L steps from U to V = U - L 1_S - E (E >= 0, |E| = (d - |S|) L,
+// U_i >= L for i in S): step j lowers every coordinate in S by 1 and takes
+// d - |S| extra units from the list of E's units sorted by coordinate; equal
+// consecutive steps form one chunk.  Every step is legal: the coordinates in S
+// stay >= 1 until the last step (the condition of Prop. 3.3 holds) and the
+// pole order stays >= n.
 void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live) {
-    const int nv = (int)X.nv, x = (int)X.d - nv;
+    const int nv = (int)X.nv, x = (int)X.d - (int)X.base - 1;
+    int inS[kMaxVars];
+    for (int t = 0; t < nv; t++) inS[t] = (int)((X.Smask >> t) & 1u);
     int rem[kMaxVars];
     int cur = 0;
-    for (int t = 0; t < nv; t++) rem[t] = U[t] - L - V[t];
+    for (int t = 0; t < nv; t++) rem[t] = U[t] - L * inS[t] - V[t];
     int prev[kMaxVars];
     int run = 0;
     auto flush = [&]() {
@@ -127,7 +130,7 @@ void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live
     };
     for (int j = 0; j < L; j++) {
         int v[kMaxVars];
-        for (int t = 0; t < nv; t++) v[t] = 1;
+        for (int t = 0; t < nv; t++) v[t] = inS[t];
         for (int u = 0; u < x; u++) {
             while (cur < nv && rem[cur] == 0) cur++;
             if (cur >= nv) break;  // cannot happen (the units sum to x L); validate_plan rejects the plan
@@ -168,7 +171,7 @@ std::vector<std::vector<int32_t>> cover_destinations(
         const PlanEntry &e = P.entries[e0 + i];
         bool ok = norm(e.U, nv) - d * L == target;
         for (int t = 0; t < nv; t++) {
-            box[i][t] = e.U[t] - L;
+            box[i][t] = e.U[t] - (((X.Smask >> t) & 1u) ? L : 0);
             if (box[i][t] < 0) ok = false;
         }
         if (ok) freeidx.push_back((int)i);
@@ -296,8 +299,8 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     P = Plan();
     if (X.b > 32) { X.error = "more than 32 basis columns"; return X.status = ZETA_ERR_UNSUPPORTED; }
     const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p, base = (int)X.base;
-    if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_COVER || policy == ZETA_POLICY_LEARNED || X.teacher)) {
-        X.error = "the cover and learned policies take S = {0..n} only";
+    if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_LEARNED || X.teacher)) {
+        X.error = "the learned policy takes S = {0..n} only";
         return X.status = ZETA_ERR_UNSUPPORTED;
     }
     // a term of pole order K has |u| = |S| - 1 + d (K - n)
@@ -430,7 +433,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
             // the learned policy plays on the cover levels: searched destinations where a term's box allows,
             // the network's directions for the others
             const bool cover = (policy == ZETA_POLICY_COVER || (policy == ZETA_POLICY_LEARNED && X.net.w)) &&
-                               t >= 2 && d >= nv;
+                               t >= 2 && d > base;
             const std::vector<int> none;
             phase(t < (int)by_level.size() ? by_level[t] : none, [](const int32_t *) { return false; },
                   [&](const PlanEntry &) { return steps; }, choose,

@@ -46,10 +46,10 @@ def test_curve_with_smaller_S_matches_oracle(ctx, policy):
     assert P == ref.P
 
 
-@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var"])
+@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var", "cover"])
 def test_cubic_surface_matches_oracle(ctx, policy):
     spec = _cubic_surfaces(7, 1, seed=7)[0]
-    ref = ozeta.compute_zeta(*spec, policy=policy, S=(3,))
+    ref = ozeta.compute_zeta(*spec, policy="p_chunk", S=(3,))     # Y does not depend on the policy
     F, Y, _ = z.zeta_frobenius(ctx, spec, policy=policy)
     assert (Y.astype(object) == ref.Y).all()
     P, _ = z.zeta_charpoly(ctx, spec, policy=policy)
@@ -71,6 +71,9 @@ def test_cubic_surface_batch(ctx):
     quintics = [zi.draw_instance("quintic_curves", i, cohomology.is_smooth)[:4] for i in range(8)]
     out, per, _ = z.zeta_batch(ctx, specs + quintics, policy="p_chunk")
     assert all(x["status"] == 0 for x in per)
+    out_cover, per_cover, _ = z.zeta_batch(ctx, specs + quintics, policy="cover")
+    assert all(x["status"] == 0 for x in per_cover)
+    assert out_cover == out
     for spec, P in zip(specs, out):
         n, d, p, c = spec
         N1 = pins.count_points(n, d, p, c, 1)

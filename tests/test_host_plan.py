@@ -346,7 +346,7 @@ def test_device_tables_for_S_all_are_the_monomial_formula(which):
             assert tab["secrow"][i][r] == (-1 if min(nu) < 0 else i * len(src) + src[nu])
 
 
-@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var"])
+@pytest.mark.parametrize("policy", ["depth_first", "p_chunk", "var_by_var", "cover"])
 def test_general_S_replay_on_a_curve_matches_oracle(policy):
     """The quartic over F_11 with S = {1, 2}: the library's section of J_S, start terms, tables and moves, replayed
     through the device formula, give the oracle's Y (which does not depend on S) and P(T)."""
@@ -378,6 +378,26 @@ def test_general_S_replay_on_cubic_surfaces_matches_oracle(p, policy):
     assert P == res.P
 
 
+def test_cover_on_cubic_surfaces_replays_exactly_and_saves_steps():
+    """The cover search with S = {3}: boxes U - L 1_S (only x_3 must fall every step), paths taking d - |S| = 2 free
+    units per step.  The replayed plan gives the oracle's Y and P(T); over 12 surfaces it plays far fewer column
+    steps than p-chunk."""
+    spec = _cubic_surface(7)
+    plan = z.zeta_plan(spec, policy="cover")
+    H = replay_moves(spec, plan, z.zeta_plan_moves(spec, policy="cover"), z.zeta_plan_tables(spec, policy="cover"))
+    F, Y, P = z.zeta_finish(spec, H)
+    res = ozeta.compute_zeta(*spec, policy="p_chunk", S=(3,))
+    assert (Y.astype(object) == res.Y).all()
+    assert P == res.P
+    tot = {"p_chunk": 0, "cover": 0}
+    for i in range(12):
+        n, d, p, c, _ = zi.draw_instance("cubic_surfaces", i, lambda *a: cohomology.is_smooth(*a)
+                                         and cohomology.is_S_smooth(*a, (3,)))
+        for pol in tot:
+            tot[pol] += z.zeta_plan((n, d, p, c), policy=pol)["game"]["column_steps"]
+    assert tot["cover"] < 0.7 * tot["p_chunk"]
+
+
 def test_general_S_refusals():
     n, d, p, c, _ = zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)
     with pytest.raises(z.ZetaError) as e:
@@ -386,10 +406,9 @@ def test_general_S_refusals():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_query((n, d, p, c), S=(3,))            # x_3 does not exist in P^2
     assert e.value.status == 1
-    for policy in ("cover", "learned"):
-        with pytest.raises(z.ZetaError) as e:
-            z.zeta_plan((n, d, p, c), policy=policy, S=(1, 2))
-        assert e.value.status == 3
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_plan((n, d, p, c), policy="learned", S=(1, 2))
+    assert e.value.status == 3
     spec = _cubic_surface(7)
     with pytest.raises(z.ZetaError) as e:
         z.zeta_query(spec, S=(0, 1, 2, 3))            # |S| = 4 > d = 3
