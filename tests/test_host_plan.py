@@ -436,3 +436,52 @@ def test_cubic_threefold_is_planned_with_S_n():
     plan = z.zeta_plan((n, d, p, c), policy="p_chunk")
     assert plan["S"] == (4,) and plan["kappa"] == 10
     assert plan["game"]["column_steps"] > 0
+
+
+def _oracle_game_counts(n, d, p, c, policy, S, r):
+    """The oracle's policy played on exponents only (no matrices): start terms of Prop. 2.1 after Tweak, combined
+    by u, then oracle.policies.play; returns (chunks, steps, merges)."""
+    from oracle.policies import play, GameLog
+    from oracle.precision import Precision
+    X = cohomology.Hypersurface(n, d, p, c)
+    basis = cohomology.cohomology_basis(X)
+    prec = Precision(n, d, p, [m for m, _ in basis], r=r)
+    us = []
+    seen = set()
+    for col, U, J, val in ozeta.frobenius_terms(X, basis, prec, S):
+        if U not in seen:
+            seen.add(U)
+            us.append(U)
+    log = GameLog()
+
+    def reduce_chunk(u, v, k, w):
+        log.chunks += 1
+        log.steps += k
+        return w
+    play(policy, [(u, None) for u in us], n, d, p, S, reduce_chunk, lambda a, b: a, log)
+    return log.chunks, log.steps, log.merges
+
+
+@pytest.mark.parametrize("case,policy", [("k3_S3", "depth_first"), ("k3_S3", "p_chunk"), ("k3_S3", "var_by_var"),
+                                         ("threefold_S4", "p_chunk")])
+def test_host_game_with_S_n_matches_the_oracle_game(case, policy):
+    # K3 surfaces admit both S = {0..3} and S = {3}; cubic threefolds only S = {4}.  At relative precision 1 the
+    # library's scheduler and the oracle's policies (separate code) play the same moves.
+    if case == "k3_S3":
+        n, d, p, c, _ = zi.draw_instance("quartic_k3", 1, cohomology.is_smooth)
+        S = (3,)
+        if not cohomology.is_S_smooth(n, d, p, c, S):
+            pytest.skip("instance not {3}-smooth")
+    else:
+        n, d, p, S = 4, 3, 11, (4,)
+        att = 0
+        while True:
+            c = zi.dense_candidate(n, d, p, 11, 0, att)
+            att += 1
+            try:
+                z.zeta_query((n, d, p, c))
+                break
+            except z.ZetaError as e:
+                assert e.status == 2
+    g = z.zeta_plan((n, d, p, c), policy=policy, r=1, S=S)["game"]
+    assert (g["chunks"], g["steps"], g["merges"]) == _oracle_game_counts(n, d, p, c, policy, S, 1)
