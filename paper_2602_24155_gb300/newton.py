@@ -72,6 +72,42 @@ def unit_roots_mod_p(P_low, p):
     return deg
 
 
+def hodge_numbers(n, d):
+    """b_m for m = 1..n: the dimension of the Jacobian ring in degree dm - n - 1, the coefficient of that degree in
+    (1 + t + ... + t^(d-2))^(n+1) (Sec. 2.3); the basis elements of pole order m have Hodge slope n - m."""
+    poly = [1]
+    for _ in range(n + 1):
+        new = [0] * (len(poly) + d - 2)
+        for i, a in enumerate(poly):
+            for j in range(d - 1):
+                new[i + j] += a
+        poly = new
+    return {m: (poly[d * m - n - 1] if 0 <= d * m - n - 1 < len(poly) else 0) for m in range(1, n + 1)}
+
+
+def first_slope(n, d):
+    """(h0, length): the first slope of the Hodge polygon, n - (largest pole order with a basis element), and the
+    number of basis elements with that slope."""
+    b = hodge_numbers(n, d)
+    m_top = max(m for m, k in b.items() if k)
+    return n - m_top, b[m_top]
+
+
+def first_slope_length(P_low, p, h0, r=1):
+    """How many reciprocal roots have p-adic valuation h0, the first Hodge slope, from P(T) computed at relative
+    precision r (a_i known mod p^(r + H(i)), H the Hodge polygon).  The Newton polygon lies on or above the Hodge
+    polygon, whose first segment has slope h0, so that number is the largest i with v_p(a_i) = h0 i, and
+    a_i mod p^(r + h0 i) decides it.  h0 = 0 (curves, K3 surfaces): the p-rank, the degree of P mod p.  h0 = 1
+    (cubic threefolds, Hodge numbers 0, 5, 5, 0): the length of the slope-one segment, the p-rank of the
+    intermediate Jacobian (Sec. 1.2); 5 is ordinary, 4 almost ordinary."""
+    best = 0
+    for i in range(1, len(P_low)):
+        a = int(P_low[i]) % p ** (r + h0 * i)
+        if a and vp(a, p) == h0 * i:
+            best = i
+    return best
+
+
 def random_hypersurfaces(n, d, p, count, seed):
     """`count` random dense coefficient vectors (C(n+d, n) values in [0, p)) from numpy's PCG64 with `seed`."""
     from math import comb
@@ -83,16 +119,18 @@ def random_hypersurfaces(n, d, p, count, seed):
 def search(ctx, n, d, p, count, seed=0, max_p_rank=None, policy="p_chunk", path="vector"):
     """Method 1: random smooth hypersurfaces of degree d in P^n over F_p.
 
-    Returns a dict: 'drawn', 'smooth', 'p_rank' (histogram over the smooth ones, from the r = 1 run), 'kept' (the
-    instances with p-rank <= max_p_rank, default: below the maximum b/2 for curves, i.e. non-ordinary), and 'strata'
-    (Newton polygon label -> list of (coefficients, P) of the kept instances, from the full-precision run)."""
+    Returns a dict: 'drawn', 'smooth', 'p_rank' (histogram over the smooth ones, from the r = 1 run, of the number
+    of roots on the first Hodge slope: the p-rank for curves, the slope-one length for cubic threefolds), 'kept'
+    (the instances with that number <= max_p_rank, default: one below the ordinary value, i.e. the non-ordinary
+    ones), and 'strata' (Newton polygon label -> list of (coefficients, P) of the kept instances, from the
+    full-precision run)."""
     specs = random_hypersurfaces(n, d, p, count, seed)
     low, per, _ = zeta_batch(ctx, specs, policy=policy, path=path, r=1)
     smooth = [i for i, x in enumerate(per) if x["status"] == 0]
-    ranks = {i: unit_roots_mod_p(low[i], p) for i in smooth}
+    h0, ordinary = first_slope(n, d)
+    ranks = {i: first_slope_length(low[i], p, h0) for i in smooth}
     if max_p_rank is None:
-        b = per[smooth[0]]["b"] if smooth else 0
-        max_p_rank = b // 2 - 1 if n == 2 else b
+        max_p_rank = ordinary - 1
     kept = [i for i in smooth if ranks[i] <= max_p_rank]
     strata = {}
     if kept:

@@ -74,3 +74,45 @@ def test_k3_heights_at_precision_one_on_the_oracle():
     low = ozeta.compute_zeta(n, d, p, c, r=1)
     assert low.P[1] % p == 0
     assert k3_height(low.P, p) >= 2
+
+
+def test_hodge_numbers_and_first_slope():
+    from paper_2602_24155_gb300.newton import hodge_numbers, first_slope
+    from oracle.cohomology import hodge_count
+    # plane quintic (g = 6), quartic K3, cubic surface, cubic threefold (0, 5, 5, 0), cubic fourfold (1, 20, 1)
+    assert hodge_numbers(2, 5) == {1: 6, 2: 6} and first_slope(2, 5) == (0, 6)
+    assert hodge_numbers(3, 4) == {1: 1, 2: 19, 3: 1} and first_slope(3, 4) == (0, 1)
+    assert hodge_numbers(3, 3) == {1: 0, 2: 6, 3: 0} and first_slope(3, 3) == (1, 6)
+    assert hodge_numbers(4, 3) == {1: 0, 2: 5, 3: 5, 4: 0} and first_slope(4, 3) == (1, 5)
+    assert hodge_numbers(5, 3) == {1: 0, 2: 1, 3: 20, 4: 1, 5: 0} and first_slope(5, 3) == (1, 1)
+    for n, d in [(2, 4), (2, 5), (3, 3), (3, 4), (3, 5), (4, 3), (5, 3)]:
+        assert sum(hodge_numbers(n, d).values()) == hodge_count(n, d)
+
+
+def test_first_slope_length_is_the_p_rank_for_curves_and_the_slope_one_length_for_threefolds():
+    from random import Random
+    from paper_2602_24155_gb300.newton import first_slope_length
+    p = 7
+    rng = Random(5)
+    for _ in range(200):                       # h0 = 0: the degree of P mod p
+        P = [1] + [rng.randrange(-500, 500) for _ in range(12)]
+        assert first_slope_length(P, p, 0) == unit_roots_mod_p(P, p)
+    # cubic threefold polygons (weight 3, b = 10, Hodge polygon H(i) = i for i <= 5, then slope 2): coefficients
+    # with v_p(a_i) on a chosen polygon (units 2 and 3 are prime to p)
+    H = [0] + list(range(1, 6)) + [5 + 2 * (i - 5) for i in range(6, 11)]
+    ordinary = [1] + [2 * p ** H[i] for i in range(1, 11)]
+    assert newton_slopes(ordinary, p) == [1] * 5 + [2] * 5
+    assert first_slope_length(ordinary, p, 1) == 5
+    almost = list(ordinary)
+    almost[5] = 3 * p ** 6                     # v(a_5) = 6: slopes 1^4 (3/2)^2 2^4, almost ordinary
+    assert newton_slopes(almost, p) == [1] * 4 + [Fraction(3, 2)] * 2 + [2] * 4
+    assert first_slope_length(almost, p, 1) == 4
+    lower = list(almost)
+    lower[4] = 3 * p ** 5                      # v(a_4) = 5, v(a_6) = 8 as well: slopes 1^3 (3/2)^4 2^3
+    lower[6] = 3 * p ** 8
+    assert newton_slopes(lower, p) == [1] * 3 + [Fraction(3, 2)] * 4 + [2] * 3
+    assert first_slope_length(lower, p, 1) == 3
+    # the truncation of an r = 1 run (a_i known mod p^(1 + H(i))) gives the same answer
+    for P in (ordinary, almost, lower):
+        low = [a % p ** (1 + H[i]) for i, a in enumerate(P)]
+        assert first_slope_length(low, p, 1) == first_slope_length(P, p, 1)
