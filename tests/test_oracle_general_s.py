@@ -205,3 +205,27 @@ def test_cubic_threefold_f11_precision_of_the_printed_modulus():
         a1 = cp[1] % p ** 3
         assert (a1 - p ** 3 if a1 > p ** 3 // 2 else a1) == pins.counts_to_charpoly_prefix(n, p, [N1])[1] == -33
         assert cp[2] % p ** 4 == 605    # a_2 = 605 from #X(F_121) = 1 786 445 (a 16-minute count, not repeated here)
+
+
+@pytest.mark.skipif(not os.environ.get("ZETA_SLOW_ORACLE"), reason="about 15 minutes; set ZETA_SLOW_ORACLE=1")
+def test_cubic_threefold_f11_full_zeta_function():
+    """The same cubic threefold at N = 5 (arithmetic mod 11^10): the columns are then known to the relative
+    precision r = (5, 6), det C is +-1, and P(T) lifts.  Its reciprocal roots all have absolute value 11^(3/2),
+    a_1 and a_2 equal those of the point counts (#X(F_11) = 1431, #X(F_121) = 1 786 445), and the first five
+    slopes are 1 (ordinary: slope-one length 5)."""
+    n, d, p = 4, 3, 11
+    att = 0
+    while True:
+        c = zi.dense_candidate(n, d, p, 11, 0, att)
+        att += 1
+        if cohomology.is_smooth(n, d, p, c) and cohomology.is_S_smooth(n, d, p, c, (4,)):
+            break
+    res = zeta.compute_zeta(n, d, p, c, policy="p_chunk", S=(4,), N=5)
+    assert res.prec.M == 10
+    P = res.P
+    assert P[:3] == [1, -33, 605]
+    assert pins.count_points(n, d, p, c, 1) == 1431
+    assert pins.root_moduli_ok(n, p, P)
+    assert pins.newton_above_hodge(n, p, P, [m for m, _ in res.basis])
+    from paper_2602_24155_gb300.newton import first_slope_length, newton_slopes
+    assert first_slope_length(P, p, 1) == 5 and newton_slopes(P, p) == [1] * 5 + [2] * 5
