@@ -209,10 +209,11 @@ def test_cubic_threefold_f11_precision_of_the_printed_modulus():
 
 @pytest.mark.skipif(not os.environ.get("ZETA_SLOW_ORACLE"), reason="about 15 minutes; set ZETA_SLOW_ORACLE=1")
 def test_cubic_threefold_f11_full_zeta_function():
-    """The same cubic threefold at N = 5 (arithmetic mod 11^10): the columns are then known to the relative
-    precision r = (5, 6), det C is +-1, and P(T) lifts.  Its reciprocal roots all have absolute value 11^(3/2),
-    a_1 and a_2 equal those of the point counts (#X(F_11) = 1431, #X(F_121) = 1 786 445), and the first five
-    slopes are 1 (ordinary: slope-one length 5)."""
+    """The same cubic threefold at N = 5 (arithmetic mod 11^10): the columns are correct to 4 and 5 digits, one
+    short of r = (5, 6), but det C is +-1 and P(T) lifts, to the polynomial that N = 6 (which reaches r; a
+    28-minute run) also gives.  Its reciprocal roots all have absolute value 11^(3/2), a_1 and a_2 equal those of
+    the point counts (#X(F_11) = 1431, #X(F_121) = 1 786 445), and the first five slopes are 1 (ordinary:
+    slope-one length 5)."""
     n, d, p = 4, 3, 11
     att = 0
     while True:
