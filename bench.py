@@ -82,7 +82,9 @@ class Clocks:
     def __init__(self, index):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # raw samples (the JSON line carries their summary); directory from ZETA_BENCH_OUT
+        out_dir = os.environ.get("ZETA_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out_dir, "clocks_rank%d.csv" % index)
 
     def start(self):
         try:
