@@ -155,6 +155,16 @@ def test_curves_Y_independent_of_S_and_policy(workload_or_p, S):
         assert res.P == ref.P
 
 
+def test_k3_surface_Y_independent_of_S():
+    # a quartic K3 surface (d = n + 1) admits S = {0..3} and S = {3}: at relative precision 1 (a truncated
+    # expansion, the same form for both) the unnormalised columns must agree exactly
+    n, d, p, c, _ = zi.draw_instance("quartic_k3", 1, cohomology.is_smooth)
+    assert cohomology.is_S_smooth(n, d, p, c, (3,))
+    a = zeta.compute_zeta(n, d, p, c, policy="p_chunk", r=1, want_P=False)
+    b = zeta.compute_zeta(n, d, p, c, policy="p_chunk", r=1, want_P=False, S=(3,))
+    assert (a.Y == b.Y).all()
+
+
 @pytest.mark.parametrize("p", [7, 13])
 def test_fermat_cubic_surface_closed_form(p):
     P = zeta.compute_zeta(3, 3, p, zi.fermat(3, 3), policy="p_chunk", S=(3,)).P
