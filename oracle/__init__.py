@@ -14,9 +14,10 @@ same loop as `reduction.horner_python` and is tested against it.
 
 Modules
   algebra     monomials, polynomials, Gaussian elimination mod p^k
-  cohomology  smoothness test, monomial basis (Sec. 2.3), section of the
-              Jacobian map, R_{u,v} (Prop. 3.3), final Griffiths-Dwork
-              reduction (Sec. 3.3 step (2))
+  cohomology  smoothness and S-smoothness tests (Definition 3.1), monomial
+              basis (Sec. 2.3), section of the map of J_S, R_{u,v} (Prop. 3.3,
+              any index set S), final Griffiths-Dwork reduction (Sec. 3.3
+              step (2))
   precision   r_m, N_m and the algorithm precision M (Sec. 2.5)
   policies    Tweak (Alg. 1), greedy direction (Alg. 3), the reduction game
               (Sec. 3.4) and the three policies of Sec. 4
