@@ -10,7 +10,7 @@ The oracle is written for a reader checking it against the paper by eye:
 exact integer arithmetic (Python big integers) mod p^M, the steps in the
 paper's order and notation, no blocking or fusion.  A small C routine
 (`horner.c`) runs Algorithm 2's inner loop for moduli below 2^63; it is the
-same loop as `reduction.horner_python` and is tested against it.
+same loop as `zeta.horner_python` and is tested against it.
 
 Modules
   algebra     monomials, polynomials, Gaussian elimination mod p^k
