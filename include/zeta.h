@@ -188,7 +188,9 @@ zeta_status zeta_frobenius(zeta_ctx *ctx, const zeta_hypersurface *hs, const zet
 zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt,
                           int64_t *P_out, zeta_stats *st);
 
-/* Many hypersurfaces (any mix of n, d, p).  Batches of 256 or more are split
+/* Many hypersurfaces (any mix of n, d, p; with opt->S_mask = 0 each takes its
+ * own default S, so curves and cubic surfaces share a launch).  Batches of
+ * 256 or more are split
  * into four sub-batches (eight from 2048) whose host setup overlaps the device
  * work of the previous one; consecutive sub-batches alternate between the
  * context's stream and a second stream of the context, so that their
