@@ -240,3 +240,12 @@ def test_cubic_threefold_f11_full_zeta_function():
     assert pins.newton_above_hodge(n, p, P, [m for m, _ in res.basis])
     from paper_2602_24155_gb300.newton import first_slope_length, newton_slopes
     assert first_slope_length(P, p, 1) == 5 and newton_slopes(P, p) == [1] * 5 + [2] * 5
+
+
+@pytest.mark.skipif(not os.environ.get("ZETA_SLOW_ORACLE"), reason="about 45 minutes; set ZETA_SLOW_ORACLE=1")
+def test_fermat_cubic_threefold_f7_closed_form():
+    """x_0^3 + ... + x_4^3 over F_7 (p = 1 mod 3), S = {4}, at the precision rules' N = 10, M = 16: P(T) equals
+    Weil's Gauss-sum formula, a closed form computed without any of the reduction."""
+    res = zeta.compute_zeta(4, 3, 7, zi.fermat(4, 3), policy="p_chunk", S=(4,))
+    assert res.prec.M == 16
+    assert res.P == pins.fermat_charpoly(4, 3, 7)
