@@ -29,13 +29,10 @@ import zeta_inputs as zi  # noqa: E402
 
 METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
 
-# DRAM traffic of the executor from one ncu capture of 456 quintics (profiles/k_execute_quintic_curves_456_learned_full.md):
-# bytes read + written per instance, per policy and path, valid for this device code only: the md5 of
-# zeta_kernels.cu up to its "Engine" separator (the kernels and their launch-shape helpers; the file as a
-# whole had md5 898edb073b9d4fdf2f90381b356b7962 at the capture).
-PROFILED_DEVICE_MD5 = "36b89dc501c2ba0a477c99aee44942dd"
-ENGINE_MARK = "// ---------------------------------------------------------------------------\n// Engine\n"
-PROFILED_DRAM_BYTES_PER_INSTANCE = {("learned", "vector"): (2.305581e9 + 2.144180e9) / 456}
+# DRAM bytes (read + written) per instance of the executor k_execute on the quintic-curve workload under the
+# learned policy, from one ncu capture of the current kernels on a small case (the capture command and its
+# scaling to a full launch are recorded with the profiles); None when no capture of these kernels exists.
+DRAM_BYTES_PER_INSTANCE = None
 WORKLOAD = "quintic_curves"
 
 
@@ -148,14 +145,23 @@ def oracle_sample(specs, cores):
     return wall, res
 
 
+def _workload_config(count):
+    """The workload of the main line, shared by both arms so that they name the same config."""
+    return {"workload": "quintic_curves_4096", "n": 2, "d": 5, "count_per_gpu": count,
+            "primes": list(zi.PRIMES_QUINTIC_CURVES), "l2": "inputs larger than L2 (HBM-resident)"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     cores = os.cpu_count() or 1
     sample_n = max(1, min(cores, 16))
     specs = _instances(0, sample_n)
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
+    # warm-up: the same process pool on the genus-3 quartic over F_11 (module imports, the C helper, the pool)
+    from oracle.cohomology import is_smooth
+    small = zi.draw_instance("quartic_curve_f11", 0, is_smooth)[:4]
+    for _ in range(args.warmup):
+        oracle_sample([small] * min(cores, sample_n), cores)
     walls = []
     steps = 0
     for _ in range(max(1, args.steps)):
@@ -164,14 +170,15 @@ def run_reference(args, rank, world):
         steps = sum(r[1] for r in res)
     wall = statistics.median(walls)
     value = sample_n / wall
-    sample = "first %d instances of %s (primes %s), %d processes, oracle as it stands" % (
-        sample_n, WORKLOAD, sorted(set(s[2] for s in specs)), min(cores, sample_n))
+    sample = ("first %d instances of %s (primes %s), %d processes, oracle as it stands; each warm-up step runs "
+              "the pool on the genus-3 quartic over F_11" % (
+                  sample_n, WORKLOAD, sorted(set(s[2] for s in specs)), min(cores, sample_n)))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "zeta/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int (exact big integers)", "data": "synthetic",
         "steps_per_s": steps / wall,
-        "config": {"workload": "quintic_curves_4096", "sample": sample_n},
+        "config": _workload_config(args.count),
         "cpu_baseline": {"value": value, "unit": "zeta/s", "cores": min(cores, sample_n), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "zeta/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -278,6 +285,8 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "vector", "gemm"],
                     help="auto: the autotuner times the launch configurations on a sample of the batch first")
     ap.add_argument("--count", type=int, default=zi.WORKLOADS[WORKLOAD]["count"])
+    ap.add_argument("--policy-count", type=int, default=1024,
+                    help="instances of the sub-batch on which every policy is timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-k3", action="store_true", help="skip the K3 height survey (512 surfaces, precision 1)")
     ap.add_argument("--no-cubic", action="store_true",
@@ -356,16 +365,23 @@ def main():
     column_steps = tot["column_steps"] * world
     s = per[0]["s"]
 
-    # the plain policy of the paper on the same batch, for the learned-vs-plain comparison
-    policies = {args.policy: {"zeta_per_s": value, "column_steps": column_steps, "ms_per_step": ms_per_step}}
+    # the learned policy against the method without the network (cover) and the paper's three policies
+    # (Sec. 4.1-4.3), all on one sub-batch of the same workload, one device-resident launch each
+    policies = {"batch": "first %d instances of the main batch" % min(args.policy_count, args.count),
+                args.policy + "_full_batch": {"zeta_per_s": value, "column_steps": column_steps,
+                                              "ms_per_step": ms_per_step}}
     if learned is not None:
-        policies["learned"].update(learned)
-    # the paper's plain policy and the cover search on the same batch and path
-    for other in ("p_chunk", "cover"):
-        if other == args.policy:
+        policies[args.policy + "_full_batch"].update(learned)
+    sub = specs[:min(args.policy_count, args.count)]
+    P_sub = None
+    for pol in ("learned", "cover", "p_chunk", "depth_first", "var_by_var"):
+        if pol == "learned" and learned is None:
             continue
-        plan2 = z.zeta_batch_prepare(ctx, specs, policy=other, path=args.path)
-        plan2.run()
+        o = dict(opt, policy=pol, path=args.path if args.path != "auto" else "vector")
+        if pol != "learned":
+            o.pop("weights", None)
+            o.pop("hidden", None)
+        plan2 = z.zeta_batch_prepare(ctx, sub, **o)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -373,12 +389,19 @@ def main():
         plan2.run()
         e1.record(stream)
         torch.cuda.synchronize()
-        P_plain, _, tot_plain = plan2.finish()
+        P_pol, _, tot_pol = plan2.finish()
         plan2.release()
-        assert P_plain == P_warm, "policies disagree"
-        ms_plain = e0.elapsed_time(e1)
-        policies[other] = {"zeta_per_s": args.count / (ms_plain / 1000.0), "column_steps": tot_plain["column_steps"],
-                           "ms_per_step": ms_plain}
+        if P_sub is None:
+            P_sub = P_pol
+        assert P_pol == P_sub == P_warm[:len(sub)], "policies disagree"
+        ms_pol = e0.elapsed_time(e1)
+        policies[pol] = {"zeta_per_s": len(sub) / (ms_pol / 1000.0), "column_steps": tot_pol["column_steps"],
+                         "chunks": tot_pol["chunks"], "steps": tot_pol["steps"], "ms_per_launch": ms_pol,
+                         "column_steps_per_s": tot_pol["column_steps"] / (ms_pol / 1000.0)}
+    if "learned" in policies and "cover" in policies:
+        policies["network_gain_over_cover"] = {
+            "column_steps": 1 - policies["learned"]["column_steps"] / policies["cover"]["column_steps"],
+            "time": 1 - policies["learned"]["ms_per_launch"] / policies["cover"]["ms_per_launch"]}
 
     # the other recurrence path on the same batch and policy (limb-split GEMM on the tensor cores against the
     # modular matrix-vector steps on the CUDA cores)
@@ -416,12 +439,8 @@ def main():
 
     # roofline of the recurrence kernel: modular multiply-adds (s^2 per column step)
     peaks = _peaks()
-    import hashlib
-    src = open(os.path.join(ROOT, "paper_2602_24155_gb300", "csrc", "zeta_kernels.cu")).read()
-    device_code = src[:src.index(ENGINE_MARK)] if ENGINE_MARK in src else src
-    same_kernel = hashlib.md5(device_code.encode()).hexdigest() == PROFILED_DEVICE_MD5
-    per_inst = PROFILED_DRAM_BYTES_PER_INSTANCE.get((args.policy, chosen))
-    traffic = per_inst * args.count if (same_kernel and per_inst) else None
+    traffic = DRAM_BYTES_PER_INSTANCE * args.count if (DRAM_BYTES_PER_INSTANCE and args.policy == "learned"
+                                                        and chosen == "vector") else None
     ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
     macs_per_launch = tot["column_steps"] * s * s
     achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12
@@ -434,11 +453,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "steps_per_s": column_steps / (ms_per_step / 1000.0),
-        "config": {"workload": "quintic_curves_4096", "n": 2, "d": 5, "count_per_gpu": args.count,
-                   "primes": list(zi.PRIMES_QUINTIC_CURVES), "policy": args.policy, "path": chosen,
-                   "block_threads": tuning["best"]["block_threads"] if tuning else 0,
-                   "l2": "inputs larger than L2 (%.2f GB resident)" % (tot["bytes_h2d"] / 1e9),
-                   "column_steps_per_step": column_steps},
+        "config": _workload_config(args.count),
+        "run": {"policy": args.policy, "path": chosen,
+                "block_threads": tuning["best"]["block_threads"] if tuning else 0,
+                "resident_bytes": tot["bytes_h2d"], "column_steps_per_step": column_steps},
         "e2e": {"value": e2e_value, "unit": "zeta/s", "h2d_bytes_per_step": coeff_bytes + tot_e2e["bytes_h2d"],
                 "d2h_bytes_per_step": tot_e2e["bytes_d2h"] + 16 * sum(len(P) for P in P_e2e)},
         "gpu_launches": args.steps,

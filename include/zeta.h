@@ -292,14 +292,22 @@ zeta_status zeta_selftest_wait(zeta_ctx *ctx, uint32_t limit_ms, double *waited_
  *    2 s c * 8 bytes of shared memory <= 227 KB.  Larger sizes return
  *    ZETA_ERR_ARG before anything is launched.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and caches it when the lookup succeeds (a failed
+ *    lookup is retried by the next call).  cudaDeviceReset on that device
+ *    invalidates the cached address: do not call this entry point on a
+ *    device after resetting it.
+ *  - The call cannot be captured into a CUDA graph: it reads a status word
+ *    back into host memory and synchronises the stream before returning.
  *  - Every call shares the array and it keeps the last call's contents; the
  *    matrices are fully written before they are read and the status word is
  *    cleared at the start of each call.  Calls that overlap on the GPU (two
  *    streams, two host threads) race on the array: serialise them.
  *  - Allocates nothing: no cudaMalloc, cudaFree, host heap, or library
- *    allocator.  ZETA_ERR_ARG also reports a modulus outside [3, 2^60] or
- *    even (that problem's W is left unchanged). */
+ *    allocator.
+ *  - Moduli are checked on the device (the host never reads q): a problem
+ *    whose q_t is even, outside [3, 2^60], or has s >= 8 q_t is skipped (its
+ *    W_t is left unchanged), the other problems are computed, and the call
+ *    returns ZETA_ERR_ARG; the next call starts with a cleared status. */
 zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uint32_t s, uint32_t c,
                                const uint32_t *k, const uint64_t *A, const uint64_t *B,
                                uint64_t *W, const uint64_t *q);

@@ -285,16 +285,55 @@ def hasse_witt_charpoly_mod_p(n, d, p, coeffs):
 # ---------------------------------------------------------------------------
 # Weil checks on P(T)
 # ---------------------------------------------------------------------------
+def _squarefree_part(P):
+    """P / gcd(P, P') for an integer polynomial (list, constant term first), exact over Q."""
+    from fractions import Fraction
+
+    def trim(a):
+        while len(a) > 1 and a[-1] == 0:
+            a = a[:-1]
+        return a
+
+    def divmod_poly(a, b):
+        a = [Fraction(x) for x in a]
+        q = [Fraction(0)] * max(1, len(a) - len(b) + 1)
+        while len(a) >= len(b) and any(a):
+            c = a[-1] / b[-1]
+            k = len(a) - len(b)
+            q[k] = c
+            for i, bi in enumerate(b):
+                a[i + k] -= c * bi
+            a = trim(a[:-1]) if len(a) > 1 else a
+        return trim(q), trim(a)
+
+    A = trim([Fraction(x) for x in P])
+    D = trim([i * A[i] for i in range(1, len(A))]) or [Fraction(0)]
+    g, h = A, D
+    while any(h):
+        _, r = divmod_poly(g, h)
+        g, h = h, r
+    g = [x / g[-1] for x in g]
+    q, r = divmod_poly(A, g)
+    assert not any(r)
+    return q
+
+
 def root_moduli_ok(n, p, P, tol=1e-20, dps=60):
-    """Every reciprocal root of P has absolute value p^{(n-1)/2}."""
+    """Every reciprocal root of P has absolute value p^{(n-1)/2}.
+
+    Repeated roots (p zeta with zeta a root of unity occurs several times on
+    special surfaces) are removed first: the roots of the square-free part
+    P / gcd(P, P') are the distinct roots of P."""
     import mpmath
     mpmath.mp.dps = dps
-    b = len(P) - 1
-    # reciprocal roots alpha are roots of T^b P(1/T) = sum a_i T^{b-i}
-    coeffs = [mpmath.mpf(a) for a in P]  # highest degree first for polyroots of reversed
+    Q = _squarefree_part(P)
+    # reciprocal roots alpha of P are the roots of T^b P(1/T) = sum a_i T^{b-i}
+    coeffs = [mpmath.mpf(x.numerator) / x.denominator for x in Q]
+    if len(coeffs) == 1:
+        return True
     roots = mpmath.polyroots(coeffs, maxsteps=400, extraprec=400)
     target = mpmath.mpf(p) ** (mpmath.mpf(n - 1) / 2)
-    return all(abs(abs(r) / target - 1) < mpmath.mpf(10) ** -12 for r in roots) and len(roots) == b
+    return all(abs(abs(r) / target - 1) < mpmath.mpf(10) ** -12 for r in roots) and len(roots) == len(Q) - 1
 
 
 def newton_above_hodge(n, p, P, pole_orders):

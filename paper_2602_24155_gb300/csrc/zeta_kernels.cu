@@ -236,7 +236,7 @@ namespace zeta {
 struct DInst {
     ModQ Q;
     uint32_t n, d, b, s, nv;
-    uint32_t sec_cols, h_rows, kappa;
+    uint32_t sec_rows, sec_cols, h_rows, kappa;
     uint32_t tab;          // table set index
     uint64_t sec_off;      // into sec pool
     uint32_t phase_off;    // into the phase offset pool: nphases + 1 entry offsets
@@ -254,12 +254,6 @@ struct DTab {
 struct DChain {
     int32_t U[kMaxVars];
     uint32_t term_begin, term_end;
-};
-
-struct DItem {
-    uint32_t inst;
-    uint32_t chain_begin, chain_end;
-    uint32_t slot;         // partial H slot
 };
 
 struct DEntry {
@@ -285,24 +279,6 @@ __device__ __forceinline__ int dev_rank(const int *ex, int nv, int deg) {
         rem -= ex[i];
     }
     return idx;
-}
-
-// Algorithm 3 (greedy v) with S = {0..n}, and the largest chunk of Sec. 4.2.
-__device__ void greedy_chunk(const int *U, int nv, int n, int d, int *v, int *k_out) {
-    int i = d;
-    for (int t = 0; t < nv; t++) v[t] = 0;
-    for (int t = 0; t < nv && i > 0; t++)
-        if (U[t] != 0) { v[t] = 1; i--; }
-    while (i > 0) {
-        for (int t = 0; t < nv && i > 0; t++)
-            if (v[t] < U[t]) { v[t]++; i--; }
-    }
-    int norm = 0;
-    for (int t = 0; t < nv; t++) norm += U[t];
-    int k = (norm - n) / d;
-    for (int t = 0; t < nv; t++)
-        if (v[t] > 0) k = min(k, U[t] / v[t]);
-    *k_out = k;
 }
 
 // Matrices M and A go to shared memory when both fit in this budget.
@@ -571,6 +547,10 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
     }
 }
 
+}  // namespace zeta
+#include "zeta_cluster.cuh"
+namespace zeta {
+
 // Kernel-level Algorithm 2 on independent problems (zeta_horner_device):
 // the same block routine as the chain kernel.
 template <int CPT, bool MSMEM>
@@ -820,6 +800,9 @@ struct DeviceBatch {
     int grid = 1, threads = 256;
     bool msmem = true;
     bool tc = false;
+    bool cluster = false;      // k_execute_cluster (instances with s > kClusterMinS)
+    int cl = 1;                // CTAs per cluster
+    int smax = 0, cmax = 0;    // largest s and b of the batch (cluster shared-memory carve)
     size_t smem = 0, scratch_stride = 0, blocks_stride = 0, h_stride = 0;
     uint64_t bytes = 0, bytes_h2d = 0, bytes_d2h = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // around each recurrence launch
@@ -925,7 +908,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         std::memset(&I, 0, sizeof(I));
         I.Q = make_modq(X->q);
         I.n = X->n; I.d = X->d; I.b = X->b; I.s = X->s; I.nv = X->nv;
-        I.sec_cols = X->sec_cols; I.h_rows = X->h_rows; I.kappa = X->kappa;
+        I.sec_rows = X->sec_rows; I.sec_cols = X->sec_cols; I.h_rows = X->h_rows; I.kappa = X->kappa;
         I.tab = tab_of[key];
         I.sec_off = secpool.size();
         {
@@ -986,6 +969,18 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     UP(dinst, d_inst);
     UP(tabs, d_tabs);
     UP(tabpool, d_tabpool);
+    const bool use_cluster = path == ZETA_PATH_VECTOR && max_s > kClusterMinS;
+    if (use_cluster) {
+        // the cluster executor reads each section column gamma as one contiguous run of rows (i, nu)
+        std::vector<uint64_t> secT(secpool.size());
+        for (size_t ii = 0; ii < batch.size(); ii++) {
+            const DInst &I = dinst[ii];
+            for (uint32_t r = 0; r < I.sec_rows; r++)
+                for (uint32_t c = 0; c < I.sec_cols; c++)
+                    secT[I.sec_off + (size_t)c * I.sec_rows + r] = secpool[I.sec_off + (size_t)r * I.sec_cols + c];
+        }
+        secpool.swap(secT);
+    }
     UP(secpool, d_sec);
     UP(dchains, d_chains);
     UP(dterms, d_terms);
@@ -1005,7 +1000,60 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         return ZETA_ERR_UNSUPPORTED;
     }
     B->tc = path == ZETA_PATH_GEMM;
+    B->smax = max_s;
+    B->cmax = max_c;
     const void *kfn;
+    if (use_cluster) {
+        // the smallest cluster whose CTAs hold their rows of M and both W buffers in shared memory
+        int cl = 1;
+        while (cl <= 16 && cl_smem(max_s, max_c, (max_s + cl - 1) / cl) > (size_t)220 * 1024) cl *= 2;
+        if (cl > 16) {
+            err = "step matrices too large for a cluster of 16 CTAs";
+            engine_release(B);
+            return ZETA_ERR_UNSUPPORTED;
+        }
+        const int R = (max_s + cl - 1) / cl;
+        B->cluster = true;
+        B->cl = cl;
+        B->smem = cl_smem(max_s, max_c, R);
+        B->msmem = true;
+        B->threads = kClThreads;
+        kfn = (const void *)k_execute_cluster;
+        CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
+        if (cl > 8) CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(cl * e->sms));
+        cfg.blockDim = dim3((unsigned)B->threads);
+        cfg.dynamicSmemBytes = B->smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, kfn, &cfg));
+        if (nclusters < 1) {
+            err = "no cluster of this size fits an SM group";
+            engine_release(B);
+            return ZETA_ERR_UNSUPPORTED;
+        }
+        nclusters = (int)std::min<size_t>((size_t)nclusters, batch.size());
+        B->grid = nclusters * cl;
+        B->scratch_stride = (size_t)R * max_s;  // this CTA's rows of A
+        B->blocks_stride = 2 * std::max<size_t>(max_block_words, 1);
+        B->h_stride = (size_t)max_h * max_c;
+#define AL(count, ptr) if ((st = dev_alloc(B, count, &B->ptr, err))) { engine_release(B); return st; }
+        AL(B->scratch_stride * B->grid, d_scratch);
+        AL(B->blocks_stride * nclusters, d_blocks);
+        AL(B->h_stride * batch.size(), d_H);
+        AL(16, d_queue);
+        AL(8, d_counters);
+#undef AL
+        *out = B;
+        return ZETA_OK;
+    }
     if (B->tc) {
         // Ms/As are replaced by the GEMM operands; at most two blocks per SM
         // (their accumulators fill the 512 TMEM columns)
@@ -1059,7 +1107,29 @@ static cudaError_t enqueue_batch(DeviceBatch *B, cudaStream_t st) {
         B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
         B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
         B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
-    if (B->tc) LAUNCH(false, true);
+    if (B->cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = B->cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)B->grid);
+        cfg.blockDim = dim3((unsigned)B->threads);
+        cfg.dynamicSmemBytes = B->smem;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ce = cudaLaunchKernelEx(&cfg, k_execute_cluster, (const DInst *)B->d_inst, (const DTab *)B->d_tabs,
+                                (const int32_t *)B->d_tabpool, (const uint64_t *)B->d_sec, (const DChain *)B->d_chains,
+                                (const Term *)B->d_terms, (const uint32_t *)B->d_phases,
+                                (const DEntry *)B->d_entries, (const DChunk *)B->d_chunks,
+                                (const uint32_t *)B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch,
+                                B->scratch_stride, B->d_blocks, B->blocks_stride, B->d_H, B->h_stride,
+                                B->d_counters, B->smax, B->cmax);
+        if (ce != cudaSuccess) return ce;
+    }
+    else if (B->tc) LAUNCH(false, true);
     else if (B->msmem) LAUNCH(true, false);
     else LAUNCH(false, false);
 #undef LAUNCH
@@ -1297,19 +1367,28 @@ __global__ void __launch_bounds__(512) k_horner_problems_static(
 
 namespace {
 constexpr int kMaxDevices = 64;
-uint64_t *g_static_ptr[kMaxDevices];
-std::once_flag g_static_once[kMaxDevices];
-cudaError_t g_static_err[kMaxDevices];
+std::mutex g_static_mu;
+uint64_t *g_static_ptr[kMaxDevices];  // cached only after a successful lookup
 }  // namespace
 
-// Device address of g_static_scratch on the current device (set up once per device).
+// Device address of g_static_scratch on the current device.  The lookup runs
+// on the first call on a device and is cached only when it succeeds, so a
+// failed first call (for example one made during a stream capture) is
+// retried by the next call.
 static cudaError_t static_scratch(int dev, uint64_t **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_static_once[dev], [dev]() {
-        g_static_err[dev] = cudaGetSymbolAddress((void **)&g_static_ptr[dev], g_static_scratch);
-    });
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        uint64_t *ptr = nullptr;
+        const cudaError_t ce = cudaGetSymbolAddress((void **)&ptr, g_static_scratch);
+        if (ce != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return ce != cudaSuccess ? ce : cudaErrorInvalidSymbol;
+        }
+        g_static_ptr[dev] = ptr;
+    }
     *out = g_static_ptr[dev];
-    return g_static_err[dev];
+    return cudaSuccess;
 }
 
 }  // namespace zeta
@@ -1348,5 +1427,3 @@ extern "C" zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uin
     return flag ? ZETA_ERR_ARG : ZETA_OK;
 }
 
-namespace zeta {
-}  // namespace zeta

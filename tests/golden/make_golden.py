@@ -1,11 +1,15 @@
 """Writes the stored expected values under tests/golden/ from the oracle alone.
 
-Run from the repository root:  python tests/golden/make_golden.py
+Run from the repository root:  python tests/golden/make_golden.py [k3]
 Each value is produced by oracle/ (which the point-count and closed-form
-tests pin); nothing here touches the CUDA path.
+tests pin); nothing here touches the CUDA path.  `k3` writes the
+full-precision P(T) of three quartic K3 surfaces (tens of minutes of CPU per
+surface, one process each).
 """
+import multiprocessing as mp
 import os
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
@@ -27,5 +31,35 @@ def main():
         fh.write("P: %s\n" % " ".join(map(str, res.P)))
 
 
+# quartic K3 workload members with their character: sparse over F_7, dense over F_13, dense over F_7
+K3_GOLDEN = [9, 2, 0]
+
+
+def _k3_one(i):
+    n, d, p, c, att = zi.draw_instance("quartic_k3", i, cohomology.is_smooth)
+    t = time.time()
+    res = zeta.compute_zeta(n, d, p, c, policy="p_chunk")
+    return i, n, d, p, c, res.prec, [int(x) for x in res.P], time.time() - t
+
+
+def k3_main():
+    with mp.get_context("spawn").Pool(len(K3_GOLDEN)) as pool:
+        rows = pool.map(_k3_one, K3_GOLDEN)
+    with open(os.path.join(HERE, "quartic_k3_full.txt"), "w") as fh:
+        fh.write("# quartic K3 surfaces of the quartic_k3 workload (seed 2) at the full precision of the oracle's\n")
+        fh.write("# rules (r_m, N_m, M); P(T) = det(1 - T F) of degree 21, Sec. 2.1; written by make_golden.py k3\n")
+        for i, n, d, p, c, prec, P, secs in rows:
+            fh.write("instance: %d\n" % i)
+            fh.write("n d p: %d %d %d\n" % (n, d, p))
+            fh.write("coeffs: %s\n" % " ".join(map(str, c)))
+            fh.write("r_m N_m M: %s %s %d\n" % (" ".join("r%d=%d" % kv for kv in sorted(prec.r.items())),
+                                              " ".join("N%d=%d" % kv for kv in sorted(prec.N.items())), prec.M))
+            fh.write("oracle seconds: %.0f\n" % secs)
+            fh.write("P: %s\n" % " ".join(map(str, P)))
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "k3":
+        k3_main()
+    else:
+        main()

@@ -204,3 +204,22 @@ def test_D_coefficients_recombine_the_binomial_series():
             lhs = sum(zeta.D_coeff(j, m, N) * y ** j for j in range(N))
             rhs = sum(sympy.binomial(-m, i) * (y - 1) ** i for i in range(N))
             assert sympy.expand(lhs - rhs) == 0
+
+
+def test_weil_root_check_with_repeated_roots():
+    # products of (1 - alpha T) with known reciprocal roots: repeated roots of modulus p pass, one root of
+    # another modulus fails; the square-free part keeps each distinct root once
+    from numpy.polynomial import polynomial as npoly
+    from oracle import pins
+
+    def prod(factors):
+        P = [1]
+        for f in factors:
+            P = [int(x) for x in npoly.polymul(P, f)]
+        return P
+    P = prod([[1, -7], [1, -7], [1, 7], [1, 0, -49], [1, 0, 49]])   # roots 7, 7, -7, +-7, +-7i
+    assert pins.root_moduli_ok(3, 7, P)
+    Q = pins._squarefree_part(P)
+    assert len(Q) - 1 == 4                                            # 7, -7, 7i, -7i
+    assert not pins.root_moduli_ok(3, 7, prod([[1, -7], [1, -7], [1, -5]]))
+    assert not pins.root_moduli_ok(3, 7, prod([[1, 0, -49], [1, -8]]))
