@@ -191,8 +191,28 @@ __device__ int cl_horner(int s, int c, int k, int row0, int nrows, uint64_t *Ms,
         }
         __syncthreads();  // this CTA's reads of M for the step are done
         cl_arrive();
-        if (step + 1 < k)
-            for (int e = threadIdx.x; e < nms; e += nt) Ms[e] = submod(Ms[e], Ag[e], Q.q);
+        if (step + 1 < k) {
+            // M <- M - A: A streamed from global memory 16 bytes at a time, four loads in flight per thread
+            const int n2 = nms >> 1;
+            const uint4 *A4 = reinterpret_cast<const uint4 *>(Ag);
+            uint4 *M4 = reinterpret_cast<uint4 *>(Ms);
+            for (int base = (int)threadIdx.x; base < n2; base += 4 * nt) {
+                uint4 av[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (base + u * nt < n2) av[u] = __ldcg(&A4[base + u * nt]);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = base + u * nt;
+                    if (e >= n2) break;
+                    uint4 m = M4[e];
+                    const uint64_t lo = submod(((uint64_t)m.y << 32) | m.x, ((uint64_t)av[u].y << 32) | av[u].x, Q.q);
+                    const uint64_t hi = submod(((uint64_t)m.w << 32) | m.z, ((uint64_t)av[u].w << 32) | av[u].z, Q.q);
+                    M4[e] = make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+                }
+            }
+            if ((nms & 1) && threadIdx.x == 0) Ms[nms - 1] = submod(Ms[nms - 1], Ag[nms - 1], Q.q);
+        }
         __syncthreads();
         cl_wait();        // every CTA's rows of the new W have landed here
         cur ^= 1;
@@ -259,6 +279,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
         const int nrows = max(0, min(R, s - row0));
         const bool l28 = I.Q.q < (1ull << 56);
         const int lb = l28 ? 28 : 30;
+        int res_buf = 1;  // buffer holding the last result; the first entry forms its W in the other
         for (uint32_t phase = 0; phase < I.nphases; phase++) {
             uint64_t *cur = (phase & 1) ? bufB : bufA;
             uint64_t *nxt = (phase & 1) ? bufA : bufB;
@@ -274,26 +295,42 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
                 __syncthreads();
                 const int c = s_nlive;
                 const int cs = pad4(c);
-                // W (every row): the arrival block's live columns or 0, then the start terms
-                for (int e = threadIdx.x; e < s * cs; e += blockDim.x) {
-                    const int j = e / cs, lc = e - j * cs;
+                // This CTA's rows of W in the buffer the previous entry's last step read from (every CTA
+                // passed that step's barrier, so no CTA reads it any more): the arrival block's live columns
+                // or 0, plus the start terms on these rows ((row, column) is unique within a chain), then
+                // sent to every other CTA of the cluster.
+                const int src = res_buf ^ 1;
+                uint2 *Wf = src ? W1 : W0;
+                for (int e = threadIdx.x; e < nrows * cs; e += blockDim.x) {
+                    const int j = row0 + e / cs, lc = e % cs;
                     uint64_t val = 0;
                     if (E.arrival >= 0 && lc < c) val = cur[(size_t)E.arrival * s * b + (size_t)j * b + colmap[lc]];
-                    W0[e] = cl_pack(val, lb);
+                    Wf[j * cs + lc] = cl_pack(val, lb);
                 }
                 __syncthreads();
-                if (E.start_chain >= 0 && threadIdx.x == 0) {
+                if (E.start_chain >= 0) {
                     const DChain C = chains[I.chain_base + E.start_chain];
-                    for (uint32_t t = C.term_begin; t < C.term_end; t++) {
+                    for (uint32_t t = C.term_begin + threadIdx.x; t < C.term_end; t += blockDim.x) {
                         const Term tm = terms[t];
+                        if ((int)tm.row < row0 || (int)tm.row >= row0 + nrows) continue;
                         int lc = 0;
                         while (colmap[lc] != (int)tm.col) lc++;
                         const int e = (int)tm.row * cs + lc;
-                        W0[e] = cl_pack(addmod(cl_unpack(W0[e], lb), tm.coeff, I.Q.q), lb);
+                        Wf[e] = cl_pack(addmod(cl_unpack(Wf[e], lb), tm.coeff, I.Q.q), lb);
                     }
                 }
                 __syncthreads();
-                int cur_buf = 0;
+                {
+                    const uint32_t base = smem_u32(Wf) + (uint32_t)(row0 * cs * 8);
+                    const uint4 *own = reinterpret_cast<const uint4 *>(Wf + row0 * cs);
+                    for (int e = threadIdx.x; e < nrows * cs / 2; e += blockDim.x) {
+                        const uint4 val = own[e];
+                        for (uint32_t t = 0; t < ncta; t++)
+                            if (t != rank) cl_st_v4(cl_map(base + 16u * (uint32_t)e, t), val);
+                    }
+                }
+                cl_arrive();  // W's rows are sent; the first chunk's matrices are built while the others finish
+                int cur_buf = src;
                 for (uint32_t ci = E.chunk_begin; ci < E.chunk_end; ci++) {
                     const DChunk CH = chunks[I.chunk_base + ci];
                     const int k = CH.k;
@@ -331,6 +368,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
                         Ms[e] = reduce128(mL, mH, I.Q);
                     }
                     __syncthreads();
+                    if (ci == E.chunk_begin) cl_wait();  // every CTA's rows of W have landed here
                     cur_buf = l28 ? cl_horner<true>(s, c, k, row0, nrows, Ms, Ag, W0, W1, cur_buf, I.Q, ncta)
                                   : cl_horner<false>(s, c, k, row0, nrows, Ms, Ag, W0, W1, cur_buf, I.Q, ncta);
                     if (threadIdx.x == 0) {
@@ -342,6 +380,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
                     }
                     __syncthreads();
                 }
+                if (E.chunk_begin == E.chunk_end) cl_wait();
+                res_buf = cur_buf;
                 const uint2 *Rw = cur_buf ? W1 : W0;
                 if (E.dest < 0) {
                     // pole order n: this CTA's rows of x^U g / x^S added into H (distinct rows, distinct h)
@@ -375,9 +415,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
                         slot = addmod(slot, val, I.Q.q);
                     }
                 }
-                // the result is read and written back; global writes visible to the cluster
+                // the result is read (the next entry starts by overwriting the entry's state)
                 __syncthreads();
-                cl_sync();
             }
         }
     }

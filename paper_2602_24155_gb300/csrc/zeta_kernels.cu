@@ -402,9 +402,10 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                     W[e] = make_uint2((uint32_t)val & MASK30, (uint32_t)(val >> 30));
                 }
                 __syncthreads();
-                if (E.start_chain >= 0 && threadIdx.x == 0) {
+                if (E.start_chain >= 0) {
+                    // (row, column) is unique within a chain: the terms are added in parallel
                     const DChain C = chains[I.chain_base + E.start_chain];
-                    for (uint32_t t = C.term_begin; t < C.term_end; t++) {
+                    for (uint32_t t = C.term_begin + threadIdx.x; t < C.term_end; t += blockDim.x) {
                         const Term tm = terms[t];
                         int lc = 0;
                         while (colmap[lc] != (int)tm.col) lc++;
@@ -1041,7 +1042,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         }
         nclusters = (int)std::min<size_t>((size_t)nclusters, batch.size());
         B->grid = nclusters * cl;
-        B->scratch_stride = (size_t)R * max_s;  // this CTA's rows of A
+        B->scratch_stride = ((size_t)R * max_s + 1) & ~(size_t)1;  // this CTA's rows of A (16-byte aligned)
         B->blocks_stride = 2 * std::max<size_t>(max_block_words, 1);
         B->h_stride = (size_t)max_h * max_c;
 #define AL(count, ptr) if ((st = dev_alloc(B, count, &B->ptr, err))) { engine_release(B); return st; }

@@ -12,10 +12,16 @@ shared memory).  These tests pin that path:
    F_p and F_{p^2}, has every reciprocal root of absolute value p, lies on or
    above the Hodge polygon, and does not change when every N_m grows by one.
 """
+import os
+import sys
+
 import pytest
 
 import zeta_inputs as zi
 from oracle import cohomology, pins, precision, zeta as ozeta
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import k3_golden  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -99,3 +105,10 @@ def test_k3_precision_rule_is_stable_under_one_more_term(ctx, full_precision):
     P1, per1, _ = z.zeta_batch(ctx, [specs[4]], policy="p_chunk", N={m + 1: N[m] + 1 for m in range(n)})
     assert per1[0]["status"] == 0
     assert P1[0] == P[4]
+
+
+def test_k3_full_precision_equals_the_oracle(full_precision):
+    specs, P, _ = full_precision
+    by_instance = {x: P[i] for i, (kind, x) in enumerate(FULL) if kind == "k3"}
+    for g in k3_golden.load():
+        assert by_instance[g["instance"]] == g["P"], g["instance"]
