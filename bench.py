@@ -272,6 +272,50 @@ def _k3_full(z, ctx, stream, torch, count):
                                        "multiply-add (28-bit limbs, q < 2^56)"}}
 
 
+def _mixed_stream(z, ctx, stream, torch):
+    """The 64-instance mixed stream of zeta_inputs.MIXED_STREAM (a quartic curve, 24 quintic curves, 16 cubic
+    surfaces, 21 quartic K3 surfaces and two Fermat cubic threefolds: s = 28 ... 495) at full precision in one
+    persistent launch; per-instance device latency from the kernel's own %globaltimer stamps."""
+
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c))
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    specs = [zi.draw_mixed(k, accept) for k in range(len(zi.MIXED_STREAM))]
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    P, per, tot = plan.finish()
+    plan.release()
+    ms = e0.elapsed_time(e1)
+    lat = sorted(st["ms_dev_end"] for st in per)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * len(lat)))]
+    by_class = {}
+    for (n, d, p, c), st in zip(specs, per):
+        key = "n%d_d%d_s%d" % (n, d, st["s"])
+        by_class.setdefault(key, []).append(st["ms_dev_end"] - st["ms_dev_start"])
+    return {"workload": "mixed_stream_64", "composition": "1 quartic curve, 24 quintic curves, 16 cubic surfaces, "
+            "21 quartic K3 surfaces, 2 Fermat cubic threefolds (no cubic fourfolds: s = 3003 is refused)",
+            "precision": "full", "launches": tot["kernel_launches"], "ms_per_launch": ms,
+            "zeta_per_s": len(specs) / (ms / 1000.0),
+            "completed": "%d/%d" % (sum(1 for st in per if st["status"] == 0), len(specs)),
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": lat[-1],
+                           "meaning": "device time from the launch's first block start to the instance's "
+                                      "numerators written back"},
+            "busy_ms_median_by_class": {k: statistics.median(v) for k, v in sorted(by_class.items())}}
+
+
 def _cubic_survey(z, ctx, stream, torch):
     """1024 dense cubic surfaces over F_7, F_11, F_13 at full precision in one persistent launch: d = 3 < n + 1, so
     the reduction runs with S = {3} (Prop. 3.3 for a smaller index set; same kernel, section of J_S).  Parity with
@@ -341,6 +385,7 @@ def main():
     ap.add_argument("--no-k3", action="store_true", help="skip the K3 height survey (512 surfaces, precision 1)")
     ap.add_argument("--k3-count", type=int, default=76,
                     help="quartic K3 surfaces of the 512-surface workload run at full precision (0: skip)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed stream")
     ap.add_argument("--no-cubic", action="store_true",
                     help="skip the cubic-surface line (1024 surfaces, S = {3}, full precision)")
     args = ap.parse_args()
@@ -533,6 +578,11 @@ def main():
             line["k3_full"] = _k3_full(z, ctx, stream, torch, args.k3_count)
         except Exception as exc:   # reported, never a reason to lose the main line
             line["k3_full"] = {"error": repr(exc)[:200]}
+    if rank == 0 and world == 1 and not args.no_mixed:
+        try:
+            line["mixed_stream"] = _mixed_stream(z, ctx, stream, torch)
+        except Exception as exc:   # reported, never a reason to lose the main line
+            line["mixed_stream"] = {"error": repr(exc)[:200]}
     if rank == 0 and world == 1 and not args.no_cubic:
         try:
             line["cubic_surfaces"] = _cubic_survey(z, ctx, stream, torch)

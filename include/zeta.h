@@ -141,6 +141,13 @@ typedef struct {
     uint64_t kernel_launches;/* launches of the recurrence kernel covered by ms_kernel */
     uint64_t bytes_h2d;      /* bytes copied host -> device (start terms, sections, tables) */
     uint64_t bytes_d2h;      /* bytes copied device -> host (numerators) */
+    /* Device latency of the instance inside its persistent launch (batches;
+     * per instance only): the times, in ms after the launch's first block
+     * started, at which a block (or cluster) took the instance from the queue
+     * and at which its numerators were written back.  The instance's result
+     * is complete on the device at ms_dev_end. */
+    double ms_dev_start;
+    double ms_dev_end;
 } zeta_stats;
 
 typedef struct zeta_ctx zeta_ctx;
@@ -353,16 +360,29 @@ zeta_status zeta_mlp_train(zeta_ctx *ctx, uint32_t hidden, float *params, const 
                            uint32_t batch_groups, float lr, float *final_loss);
 
 /* Training decisions of one instance, generated by the game itself (host
- * only): the p-chunk game is played with a teacher rule (the legal direction
- * with the longest chunk, ties to the smallest exponent reached), which
- * combines more terms than Algorithm 3; every chunk decision with two or more
- * legal directions is a group of candidate rows (row 0: Algorithm 3's choice)
- * labelled with the teacher's choice; costs[row] = the teacher's chunk length
- * minus the row's.  Two calls: with NULL buffers to read ngroups and ncand,
- * then with buffers of ncand * ZETA_POLICY_FEATURES floats, ngroups+1 offsets,
- * ngroups labels, ncand costs. */
+ * only).  The cover game (ZETA_POLICY_COVER) is played with Algorithm 3 and its
+ * chunk decisions with two or more legal directions are recorded; for a
+ * sample of at most 128 of them, every legal direction is tried in a rollout
+ * of the whole game (the same cover game, Algorithm 3 elsewhere) whose cost is
+ * the plan's column steps plus 10 per chunk (the measured setup cost of a
+ * chunk in column steps).  Each sampled decision is a group of candidate rows
+ * (row 0: Algorithm 3's choice) labelled with the cheapest direction (ties to
+ * row 0); costs[row] = the row's rollout cost minus the label's.  Two calls:
+ * with NULL buffers to read ngroups and ncand, then with buffers of
+ * ncand * ZETA_POLICY_FEATURES floats, ngroups+1 offsets, ngroups labels,
+ * ncand costs (the calling thread keeps the last instance's result between
+ * the two calls, so the rollouts run once).  ZETA_ERR_UNSUPPORTED unless
+ * S = {0..n} and n <= 3. */
 zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options *opt, size_t *ngroups,
                                 size_t *ncand, float *X, uint32_t *group_off, uint32_t *labels, int32_t *costs);
+
+/* Scores of n rows computed on the host: the forward pass the scheduler runs
+ * for ZETA_POLICY_LEARNED (the same network as zeta_mlp_forward; float
+ * arithmetic in a fixed order).  The scheduler scores a few legal directions
+ * per decision between other host work, where a device launch per decision
+ * would cost more than the network (a few hundred multiply-adds).  hidden in
+ * 1..512; host buffers. */
+zeta_status zeta_mlp_forward_host(uint32_t hidden, const float *params, const float *X, size_t n, float *scores);
 
 /* ---------------------------------------------------------------------------
  * Host-only entry points (no device needed): the setup and finishing steps

@@ -31,7 +31,7 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
            "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait", "zeta_plan_moves",
-           "zeta_plan_tables"]
+           "zeta_plan_tables", "zeta_mlp_forward_host"]
 FLAG_Y_ONLY = 1
 
 
@@ -71,7 +71,7 @@ class Stats(ctypes.Structure):
                 ("ms_host_setup", ctypes.c_double), ("ms_device", ctypes.c_double),
                 ("ms_host_finish", ctypes.c_double), ("ms_kernel", ctypes.c_double),
                 ("kernel_launches", ctypes.c_uint64), ("bytes_h2d", ctypes.c_uint64),
-                ("bytes_d2h", ctypes.c_uint64)]
+                ("bytes_d2h", ctypes.c_uint64), ("ms_dev_start", ctypes.c_double), ("ms_dev_end", ctypes.c_double)]
 
     def as_dict(self):
         out = {}
@@ -123,6 +123,8 @@ def _load():
     lib.zeta_mlp_init.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]
     lib.zeta_mlp_forward.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_size_t, ctypes.c_void_p]
+    lib.zeta_mlp_forward_host.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]
     lib.zeta_mlp_grad.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                   ctypes.c_void_p]
@@ -429,6 +431,15 @@ def zeta_mlp_forward(ctx, hidden, params, X):
     params = np.ascontiguousarray(params, dtype=np.float32)
     out = np.zeros(X.shape[0], dtype=np.float32)
     _check(ctx, LIB.zeta_mlp_forward(ctx, hidden, params.ctypes.data, X.ctypes.data, X.shape[0], out.ctypes.data))
+    return out
+
+
+def zeta_mlp_forward_host(hidden, params, X):
+    """Scores computed by the host forward pass the scheduler uses."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    out = np.zeros(X.shape[0], dtype=np.float32)
+    _check(None, LIB.zeta_mlp_forward_host(hidden, params.ctypes.data, X.ctypes.data, X.shape[0], out.ctypes.data))
     return out
 
 

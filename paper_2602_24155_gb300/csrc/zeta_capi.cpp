@@ -77,6 +77,8 @@ static void fill_stats(const Instance &X, zeta_stats *st, double ms_device) {
     st->ms_host_setup = X.ms_setup;
     st->ms_device = ms_device;
     st->ms_host_finish = X.ms_finish;
+    st->ms_dev_start = X.ms_dev_start;
+    st->ms_dev_end = X.ms_dev_end;
 }
 
 static zeta_options default_options() {
@@ -500,22 +502,48 @@ zeta_status zeta_plan_moves(const zeta_hypersurface *hs, const zeta_options *opt
 
 zeta_status zeta_policy_dataset(const zeta_hypersurface *hs, const zeta_options *opt, size_t *ngroups, size_t *ncand,
                                 float *X, uint32_t *group_off, uint32_t *labels, int32_t *costs) {
-    if (!hs || !ngroups || !ncand) return ZETA_ERR_ARG;
+    if (!hs || !ngroups || !ncand || !hs->coeffs) return ZETA_ERR_ARG;
     zeta_options o = opt ? *opt : default_options();
-    Instance I;
-    zeta_status st = prepare_instance(hs, &o, true, I);
-    if (st) return st;
-    std::vector<float> feat;
-    std::vector<uint32_t> goff, lab;
-    std::vector<int32_t> cost;
-    st = policy_dataset(I, feat, goff, lab, cost);
-    if (st) return st;
-    *ngroups = lab.size();
-    *ncand = cost.size();
-    if (X) std::memcpy(X, feat.data(), sizeof(float) * feat.size());
-    if (group_off) std::memcpy(group_off, goff.data(), sizeof(uint32_t) * goff.size());
-    if (labels) std::memcpy(labels, lab.data(), sizeof(uint32_t) * lab.size());
-    if (costs) std::memcpy(costs, cost.data(), sizeof(int32_t) * cost.size());
+    // the rollouts are costly: the last instance's dataset is kept per host thread, so that the sizing call
+    // and the filling call of the two-call protocol run them once
+    struct Cached {
+        std::vector<uint32_t> key;
+        std::vector<float> feat;
+        std::vector<uint32_t> goff, lab;
+        std::vector<int32_t> cost;
+    };
+    static thread_local Cached cache;
+    if (hs->n < 1 || hs->n > 7 || hs->d < 2 || hs->d > 12) return ZETA_ERR_UNSUPPORTED;
+    size_t ncoef = 1;  // C(n + d, n)
+    for (uint32_t i = 1; i <= hs->n; i++) ncoef = ncoef * (hs->d + i) / i;
+    std::vector<uint32_t> key = {hs->n, hs->d, hs->p, o.r_override, o.S_mask};
+    key.insert(key.end(), o.N_override, o.N_override + 8);
+    key.insert(key.end(), hs->coeffs, hs->coeffs + ncoef);
+    if (key != cache.key) {
+        Instance I;
+        zeta_status st = prepare_instance(hs, &o, true, I);
+        if (st) return st;
+        Cached c;
+        st = policy_dataset(I, c.feat, c.goff, c.lab, c.cost);
+        if (st) return st;
+        c.key = key;
+        cache = std::move(c);
+    }
+    *ngroups = cache.lab.size();
+    *ncand = cache.cost.size();
+    if (X) std::memcpy(X, cache.feat.data(), sizeof(float) * cache.feat.size());
+    if (group_off) std::memcpy(group_off, cache.goff.data(), sizeof(uint32_t) * cache.goff.size());
+    if (labels) std::memcpy(labels, cache.lab.data(), sizeof(uint32_t) * cache.lab.size());
+    if (costs) std::memcpy(costs, cache.cost.data(), sizeof(int32_t) * cache.cost.size());
+    return ZETA_OK;
+}
+
+zeta_status zeta_mlp_forward_host(uint32_t hidden, const float *params, const float *X, size_t n, float *scores) {
+    if (!params || (n && (!X || !scores)) || hidden == 0 || hidden > 512) return ZETA_ERR_ARG;
+    PolicyNet net;
+    net.w = params;
+    net.hidden = (int)hidden;
+    for (size_t i = 0; i < n; i++) scores[i] = policy_score(net, X + i * kPolicyFeatures);
     return ZETA_OK;
 }
 

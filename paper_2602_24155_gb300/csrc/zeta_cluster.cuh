@@ -237,22 +237,19 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
     const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
     const uint32_t *__restrict__ order, uint32_t ninst, uint32_t *__restrict__ queue,
     uint64_t *__restrict__ ascratch, size_t a_stride, uint64_t *__restrict__ blocks, size_t blocks_stride,
-    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters, int smax, int cmax) {
+    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters,
+    unsigned long long *__restrict__ stamps) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
     const uint32_t rank = cl_rank(), ncta = cl_size();
-    const int Rmax = (smax + (int)ncta - 1) / (int)ncta;
-    uint64_t *Ms = reinterpret_cast<uint64_t *>(smem_raw);
-    uint2 *W0 = reinterpret_cast<uint2 *>(smem_raw + cl_w_offset(smax, Rmax));
-    uint2 *W1 = W0 + (size_t)smax * pad4(cmax);
-    int *colmap = reinterpret_cast<int *>(W1 + (size_t)smax * pad4(cmax));
-    int *colidx = colmap + 32;
     uint64_t *Ag = ascratch + (size_t)blockIdx.x * a_stride;
     uint64_t *bufA = blocks + (size_t)cl_id() * blocks_stride;
     uint64_t *bufB = bufA + blocks_stride / 2;
     unsigned long long my_chunks = 0, my_steps = 0;
     const uint32_t item_addr0 = cl_map(smem_u32(&s_item), 0);
+    // device latency (as in k_execute): launch start, and each instance's start and end
+    if (threadIdx.x == 0) atomicMin(&stamps[2 * (size_t)ninst], global_ns());
     while (true) {
         if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
         cl_sync();
@@ -269,6 +266,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
         }
         cl_sync();  // every CTA has read the draw (rank 0 may draw again only after the instance)
         if (itx >= ninst) break;
+        if (rank == 0 && threadIdx.x == 0) stamps[2 * inst] = global_ns();
         const DTab T = tabs[I.tab];
         const int32_t *monoS = tabpool + T.monoS_off;
         const int32_t *secrow = tabpool + T.secrow_off;
@@ -277,6 +275,12 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
         const int R = (s + (int)ncta - 1) / (int)ncta;
         const int row0 = (int)rank * R;
         const int nrows = max(0, min(R, s - row0));
+        // shared memory of this instance (cl_smem(s, b, R) bytes): M rows, W0, W1, column map, column indices
+        uint64_t *Ms = reinterpret_cast<uint64_t *>(smem_raw);
+        uint2 *W0 = reinterpret_cast<uint2 *>(smem_raw + cl_w_offset(s, R));
+        uint2 *W1 = W0 + (size_t)s * pad4(b);
+        int *colmap = reinterpret_cast<int *>(W1 + (size_t)s * pad4(b));
+        int *colidx = colmap + 32;
         const bool l28 = I.Q.q < (1ull << 56);
         const int lb = l28 ? 28 : 30;
         int res_buf = 1;  // buffer holding the last result; the first entry forms its W in the other
@@ -419,6 +423,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_execute_cluster(
                 __syncthreads();
             }
         }
+        if (threadIdx.x == 0) atomicMax(&stamps[2 * inst + 1], global_ns());  // the cluster's last CTA to finish
     }
     if (rank == 0 && threadIdx.x == 0) {
         atomicAdd(&counters[0], my_chunks);

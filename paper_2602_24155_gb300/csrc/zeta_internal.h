@@ -2,6 +2,7 @@
 // kernels (zeta_kernels.cu).  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -97,7 +98,9 @@ struct Instance {
     PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
     // per level t: exponent -> terms reaching it in the p-chunk game with Algorithm 3
     std::vector<std::unordered_map<uint64_t, int>> ref_contrib;
-    bool teacher = false;       // p-chunk played with teacher_direction (training data)
+    // ZETA_POLICY_COVER with a decision hook: the hook chooses the direction of every chunk decision
+    // (U, steps left in the p-chunk, level t); false = Algorithm 3 (training-data rollouts)
+    std::function<bool(const int32_t *U, int left, int t, int *v)> hook;
     // results
     std::vector<uint64_t> H;     // h_rows x b accumulated numerators mod q
     std::vector<uint64_t> Y;     // b x b
@@ -108,6 +111,7 @@ struct Instance {
     std::string error;
     uint64_t nterms = 0, steps = 0, column_steps = 0, chunks = 0;
     double ms_setup = 0, ms_finish = 0;
+    double ms_dev_start = 0, ms_dev_end = 0;  // instance start and end in its launch (device clock)
 };
 
 // Host-side steps (zeta_host.cpp)
@@ -122,11 +126,13 @@ size_t policy_param_count(int hidden);
 // Chooses the direction of a chunk of the p-chunk of the term at U (level t of tmax,
 // `left` steps left); false when no network is set or only one direction is legal.
 bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int tmax, int *v);
-// The rule that labels the training decisions: the legal direction with the longest chunk
-// (ties: the smallest exponent reached, descending lexicographic order).
-bool teacher_direction(const Instance &X, const int32_t *U, int left, int *v);
+// Training decisions labelled by rollouts of the cover game (see zeta_learn.cpp).
+constexpr int kDatasetDecisions = 128;  // decisions sampled per instance
+constexpr int kChunkCost = 10;          // setup of one chunk in column steps (measured)
 zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<uint32_t> &group_off,
                            std::vector<uint32_t> &labels, std::vector<int32_t> &costs);
+// Host copy of the network's forward pass, used by the scheduler (zeta_mlp_forward_host).
+float policy_score(const PolicyNet &net, const float *x);
 // Plays the p-chunk game with Algorithm 3 and records, per level, how many terms reach each exponent.
 zeta_status reference_contributions(Instance &X);
 zeta_status finish_y_only(Instance &X);  // Y = Fin * H only

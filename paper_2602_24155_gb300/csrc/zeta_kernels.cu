@@ -144,14 +144,14 @@ __device__ __forceinline__ uint64_t to_mont(uint64_t a, const ModQ &Q) {
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int pad4(int c) { return (c + 3) & ~3; }
 
-template <int CPT>
+template <int CPT, bool L28 = false>
 __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *As, uint2 *W, uint2 *V,
                             const ModQ &Q) {
     static_assert(CPT == 4, "items are groups of four columns");
     const int cs = pad4(c);
     const int ngroups = cs / 4;
     const int items = s * ngroups;
-    const uint32_t MASK20 = (1u << 20) - 1, MASK30 = (1u << 30) - 1;
+    const uint32_t MASK20 = (1u << 20) - 1, MASK28 = (1u << 28) - 1, MASK30 = (1u << 30) - 1;
     // Few items (narrow W): split each item's j range between lanes l and
     // l + 16 of a warp and add the two partial sums with one shuffle round,
     // so that twice as many lanes work.  Block-uniform.
@@ -169,11 +169,12 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
             const int c0 = valid ? (it / s) * 4 : 0;
             const int jb = (jsplit && half) ? s / 2 : 0;
             const int je = !valid ? jb : ((jsplit && !half) ? s / 2 : s);
-            uint64_t S[4][6];
+            constexpr int NS = L28 ? 4 : 6;
+            uint64_t S[4][NS];
 #pragma unroll
             for (int cc = 0; cc < 4; cc++)
 #pragma unroll
-                for (int t = 0; t < 6; t++) S[cc][t] = 0;
+                for (int t = 0; t < NS; t++) S[cc][t] = 0;
             const int wstride = cs / 2;  // uint4 per W row
             const uint64_t *mp = Ms + (size_t)jb * s + r;
             const uint4 *wp = reinterpret_cast<const uint4 *>(in + c0) + (size_t)jb * wstride;
@@ -181,36 +182,56 @@ __device__ int horner_block(int s, int c, int k, uint64_t *Ms, const uint64_t *A
             for (int j = jb; j < je; j++) {
                 const uint64_t m = *mp;
                 mp += s;
-                const uint32_t m0 = (uint32_t)m & MASK20;
-                const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
-                const uint32_t m2 = (uint32_t)(m >> 40);
                 const uint4 wa = wp[0], wb = wp[1];  // columns c0, c0+1 | c0+2, c0+3
                 wp += wstride;
-                madw(S[0][0], m0, wa.x); madw(S[0][1], m0, wa.y);
-                madw(S[0][2], m1, wa.x); madw(S[0][3], m1, wa.y);
-                madw(S[0][4], m2, wa.x); madw(S[0][5], m2, wa.y);
-                madw(S[1][0], m0, wa.z); madw(S[1][1], m0, wa.w);
-                madw(S[1][2], m1, wa.z); madw(S[1][3], m1, wa.w);
-                madw(S[1][4], m2, wa.z); madw(S[1][5], m2, wa.w);
-                madw(S[2][0], m0, wb.x); madw(S[2][1], m0, wb.y);
-                madw(S[2][2], m1, wb.x); madw(S[2][3], m1, wb.y);
-                madw(S[2][4], m2, wb.x); madw(S[2][5], m2, wb.y);
-                madw(S[3][0], m0, wb.z); madw(S[3][1], m0, wb.w);
-                madw(S[3][2], m1, wb.z); madw(S[3][3], m1, wb.w);
-                madw(S[3][4], m2, wb.z); madw(S[3][5], m2, wb.w);
+                if (L28) {
+                    // q < 2^56: 28-bit limbs of M (Montgomery form) and W, four products
+                    const uint32_t m0 = (uint32_t)m & MASK28, m1 = (uint32_t)(m >> 28);
+                    madw(S[0][0], m0, wa.x); madw(S[0][1], m0, wa.y); madw(S[1][0], m0, wa.z); madw(S[1][1], m0, wa.w);
+                    madw(S[2][0], m0, wb.x); madw(S[2][1], m0, wb.y); madw(S[3][0], m0, wb.z); madw(S[3][1], m0, wb.w);
+                    madw(S[0][2], m1, wa.x); madw(S[0][3], m1, wa.y); madw(S[1][2], m1, wa.z); madw(S[1][3], m1, wa.w);
+                    madw(S[2][2], m1, wb.x); madw(S[2][3], m1, wb.y); madw(S[3][2], m1, wb.z); madw(S[3][3], m1, wb.w);
+                } else {
+                    const uint32_t m0 = (uint32_t)m & MASK20;
+                    const uint32_t m1 = (uint32_t)(m >> 20) & MASK20;
+                    const uint32_t m2 = (uint32_t)(m >> 40);
+                    madw(S[0][0], m0, wa.x); madw(S[0][1], m0, wa.y);
+                    madw(S[0][2], m1, wa.x); madw(S[0][3], m1, wa.y);
+                    madw(S[0][4], m2, wa.x); madw(S[0][5], m2, wa.y);
+                    madw(S[1][0], m0, wa.z); madw(S[1][1], m0, wa.w);
+                    madw(S[1][2], m1, wa.z); madw(S[1][3], m1, wa.w);
+                    madw(S[1][4], m2, wa.z); madw(S[1][5], m2, wa.w);
+                    madw(S[2][0], m0, wb.x); madw(S[2][1], m0, wb.y);
+                    madw(S[2][2], m1, wb.x); madw(S[2][3], m1, wb.y);
+                    madw(S[2][4], m2, wb.x); madw(S[2][5], m2, wb.y);
+                    madw(S[3][0], m0, wb.z); madw(S[3][1], m0, wb.w);
+                    madw(S[3][2], m1, wb.z); madw(S[3][3], m1, wb.w);
+                    madw(S[3][4], m2, wb.z); madw(S[3][5], m2, wb.w);
+                }
             }
             if (jsplit) {
 #pragma unroll
                 for (int cc = 0; cc < 4; cc++)
 #pragma unroll
-                    for (int t = 0; t < 6; t++) S[cc][t] += __shfl_xor_sync(0xffffffffu, S[cc][t], 16);
+                    for (int t = 0; t < NS; t++) S[cc][t] += __shfl_xor_sync(0xffffffffu, S[cc][t], 16);
                 if (!valid || half) continue;
             }
             uint2 res[4];
 #pragma unroll
             for (int cc = 0; cc < 4; cc++) {
-                const uint64_t v = fold_partials(S[cc], Q);
-                res[cc] = make_uint2((uint32_t)v & MASK30, (uint32_t)(v >> 30));
+                uint64_t v;
+                if (L28) {
+                    // X = S00 + (S01 + S10) 2^28 + S11 2^56 < s q^2 < q 2^64 (s <= 256)
+                    uint64_t lo = S[cc][0], hi = 0;
+                    add128(lo, hi, S[cc][1] << 28); hi += S[cc][1] >> 36;
+                    add128(lo, hi, S[cc][2] << 28); hi += S[cc][2] >> 36;
+                    add128(lo, hi, S[cc][3] << 56); hi += S[cc][3] >> 8;
+                    v = redc(lo, hi, Q);
+                    res[cc] = make_uint2((uint32_t)v & MASK28, (uint32_t)(v >> 28));
+                } else {
+                    v = fold_partials(S[cc], Q);
+                    res[cc] = make_uint2((uint32_t)v & MASK30, (uint32_t)(v >> 30));
+                }
             }
             uint4 *o = reinterpret_cast<uint4 *>(out + r * cs + c0);
             o[0] = make_uint4(res[0].x, res[0].y, res[1].x, res[1].y);
@@ -317,11 +338,15 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
     const uint32_t *__restrict__ phase_pool, const DEntry *__restrict__ entries, const DChunk *__restrict__ chunks,
     const uint32_t *__restrict__ order, uint32_t ninst, uint32_t *__restrict__ queue,
     uint64_t *__restrict__ scratch, size_t scratch_stride, uint64_t *__restrict__ blocks, size_t blocks_stride,
-    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters) {
+    uint64_t *__restrict__ Hout, size_t h_stride, unsigned long long *__restrict__ counters,
+    unsigned long long *__restrict__ stamps) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ int sU[kMaxVars], sv[kMaxVars], s_nlive;
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_tmem;
+    // device latency: stamps[2 ninst] = the launch's earliest block start, stamps[2i], stamps[2i+1] = start
+    // and end of instance i (%globaltimer, ns)
+    if (threadIdx.x == 0) atomicMin(&stamps[2 * (size_t)ninst], global_ns());
     __shared__ __align__(8) uint64_t s_mbar[2];
     __shared__ uint2 s_ct[2 * kTcMaxL], s_ct_odd[2 * 16];
     __shared__ int s_abort[2];
@@ -343,6 +368,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
         __syncthreads();
         if (itx >= ninst) break;
         const uint32_t inst = order[itx];
+        if (threadIdx.x == 0) stamps[2 * inst] = global_ns();
         const DInst I = insts[inst];
         const DTab T = tabs[I.tab];
         const int s = (int)I.s, b = (int)I.b, nv = (int)I.nv, n = (int)I.n, d = (int)I.d;
@@ -377,7 +403,10 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
         int *colidx = colmap + b;
         uint64_t *bufA = blocks + (size_t)blockIdx.x * blocks_stride;
         uint64_t *bufB = bufA + blocks_stride / 2;
-        const uint32_t MASK30 = (1u << 30) - 1;
+        // W limbs: 28 bits when q < 2^56 on the CUDA-core path (four products per entry), else 30 bits
+        const bool l28 = !TC && I.Q.q < (1ull << 56) && s <= 256;
+        const int lb = l28 ? 28 : 30;
+        const uint32_t LMASK = (1u << lb) - 1u;
         for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) Hs[e] = 0;
         for (uint32_t phase = 0; phase < I.nphases; phase++) {
             uint64_t *cur = (phase & 1) ? bufB : bufA;
@@ -399,7 +428,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                     const int j = e / cs, lc = e - j * cs;
                     uint64_t val = 0;
                     if (E.arrival >= 0 && lc < c) val = cur[(size_t)E.arrival * s * b + (size_t)j * b + colmap[lc]];
-                    W[e] = make_uint2((uint32_t)val & MASK30, (uint32_t)(val >> 30));
+                    W[e] = make_uint2((uint32_t)val & LMASK, (uint32_t)(val >> lb));
                 }
                 __syncthreads();
                 if (E.start_chain >= 0) {
@@ -410,9 +439,9 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                         int lc = 0;
                         while (colmap[lc] != (int)tm.col) lc++;
                         const int e = (int)tm.row * cs + lc;
-                        const uint64_t old = ((uint64_t)W[e].y << 30) | W[e].x;
+                        const uint64_t old = ((uint64_t)W[e].y << lb) | W[e].x;
                         const uint64_t nw = addmod(old, tm.coeff, I.Q.q);
-                        W[e] = make_uint2((uint32_t)nw & MASK30, (uint32_t)(nw >> 30));
+                        W[e] = make_uint2((uint32_t)nw & LMASK, (uint32_t)(nw >> lb));
                     }
                 }
                 __syncthreads();
@@ -483,8 +512,10 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                             Ms[(size_t)j * s + r] = reduce128(mL, mH, I.Q);
                         }
                         __syncthreads();
-                        if (cur_buf == 0) res = horner_block<CPT>(s, c, k, Ms, As, W, V, I.Q);
-                        else res = horner_block<CPT>(s, c, k, Ms, As, V, W, I.Q);
+                        if (l28) res = cur_buf == 0 ? horner_block<CPT, true>(s, c, k, Ms, As, W, V, I.Q)
+                                                    : horner_block<CPT, true>(s, c, k, Ms, As, V, W, I.Q);
+                        else res = cur_buf == 0 ? horner_block<CPT, false>(s, c, k, Ms, As, W, V, I.Q)
+                                                : horner_block<CPT, false>(s, c, k, Ms, As, V, W, I.Q);
                     }
                     cur_buf ^= res;
                     if (threadIdx.x == 0) {
@@ -500,7 +531,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                     const int hdeg = d * n - n - 1;
                     for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
                         const int j = e / c, lc = e % c;
-                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << 30) | R[j * cs + lc].x;
+                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << lb) | R[j * cs + lc].x;
                         if (!val) continue;
                         int g[kMaxVars];
                         bool ok = true;
@@ -522,7 +553,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
                     }
                     for (int e = threadIdx.x; e < s * c; e += blockDim.x) {
                         const int j = e / c, lc = e % c;
-                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << 30) | R[j * cs + lc].x;
+                        const uint64_t val = ((uint64_t)R[j * cs + lc].y << lb) | R[j * cs + lc].x;
                         uint64_t &slot = dst[(size_t)j * b + colmap[lc]];
                         slot = addmod(slot, val, I.Q.q);
                     }
@@ -534,6 +565,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
         uint64_t *out = Hout + (size_t)inst * h_stride;
         for (int e = threadIdx.x; e < (int)I.h_rows * b; e += blockDim.x) out[e] = Hs[e];
         __syncthreads();
+        if (threadIdx.x == 0) stamps[2 * inst + 1] = global_ns();
     }
     if (false) {
     aborted:  // an MMA wait timed out: flag it, wait once more for the MMAs in flight, stop
@@ -798,6 +830,7 @@ struct DeviceBatch {
     uint32_t *d_order = nullptr, *d_queue = nullptr;
     uint64_t *d_scratch = nullptr, *d_blocks = nullptr, *d_H = nullptr;
     unsigned long long *d_counters = nullptr;
+    unsigned long long *d_stamps = nullptr;  // 2 per instance + the launch start (device latency)
     int grid = 1, threads = 256;
     bool msmem = true;
     bool tc = false;
@@ -1005,18 +1038,29 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     B->cmax = max_c;
     const void *kfn;
     if (use_cluster) {
-        // the smallest cluster whose CTAs hold their rows of M and both W buffers in shared memory
+        // the smallest cluster whose CTAs hold their rows of M and both W buffers in shared memory, for every
+        // instance of the batch
+        auto need = [&](int cl, size_t *a_words) {
+            size_t bytes = 0, aw = 0;
+            for (Instance *X : batch) {
+                const int R = ((int)X->s + cl - 1) / cl;
+                bytes = std::max(bytes, cl_smem((int)X->s, (int)X->b, R));
+                aw = std::max(aw, (size_t)R * X->s);
+            }
+            if (a_words) *a_words = aw;
+            return bytes;
+        };
         int cl = 1;
-        while (cl <= 16 && cl_smem(max_s, max_c, (max_s + cl - 1) / cl) > (size_t)220 * 1024) cl *= 2;
+        while (cl <= 16 && need(cl, nullptr) > (size_t)220 * 1024) cl *= 2;
         if (cl > 16) {
             err = "step matrices too large for a cluster of 16 CTAs";
             engine_release(B);
             return ZETA_ERR_UNSUPPORTED;
         }
-        const int R = (max_s + cl - 1) / cl;
+        size_t a_words = 0;
         B->cluster = true;
         B->cl = cl;
-        B->smem = cl_smem(max_s, max_c, R);
+        B->smem = need(cl, &a_words);
         B->msmem = true;
         B->threads = kClThreads;
         kfn = (const void *)k_execute_cluster;
@@ -1042,7 +1086,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         }
         nclusters = (int)std::min<size_t>((size_t)nclusters, batch.size());
         B->grid = nclusters * cl;
-        B->scratch_stride = ((size_t)R * max_s + 1) & ~(size_t)1;  // this CTA's rows of A (16-byte aligned)
+        B->scratch_stride = (a_words + 1) & ~(size_t)1;  // this CTA's rows of A (16-byte aligned)
         B->blocks_stride = 2 * std::max<size_t>(max_block_words, 1);
         B->h_stride = (size_t)max_h * max_c;
 #define AL(count, ptr) if ((st = dev_alloc(B, count, &B->ptr, err))) { engine_release(B); return st; }
@@ -1051,6 +1095,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
         AL(B->h_stride * batch.size(), d_H);
         AL(16, d_queue);
         AL(8, d_counters);
+        AL(2 * batch.size() + 1, d_stamps);
 #undef AL
         *out = B;
         return ZETA_OK;
@@ -1093,6 +1138,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
     AL(B->h_stride * batch.size(), d_H);
     AL(16, d_queue);
     AL(8, d_counters);
+    AL(2 * batch.size() + 1, d_stamps);
 #undef AL
     *out = B;
     return ZETA_OK;
@@ -1102,12 +1148,15 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
 static cudaError_t enqueue_batch(DeviceBatch *B, cudaStream_t st) {
     cudaError_t ce = cudaMemsetAsync(B->d_queue, 0, 16 * sizeof(uint32_t), st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(B->d_counters, 0, 8 * sizeof(unsigned long long), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(B->d_stamps, 0, 2 * B->insts.size() * sizeof(unsigned long long), st);
+    if (ce == cudaSuccess)
+        ce = cudaMemsetAsync(B->d_stamps + 2 * B->insts.size(), 0xff, sizeof(unsigned long long), st);
     if (ce != cudaSuccess) return ce;
 #define LAUNCH(MS, TC)                                                                                      \
     k_execute<4, MS, TC><<<B->grid, B->threads, B->smem, st>>>(                                             \
         B->d_inst, B->d_tabs, B->d_tabpool, B->d_sec, B->d_chains, B->d_terms, B->d_phases, B->d_entries,    \
         B->d_chunks, B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch, B->scratch_stride,     \
-        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters)
+        B->d_blocks, B->blocks_stride, B->d_H, B->h_stride, B->d_counters, B->d_stamps)
     if (B->cluster) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -1127,7 +1176,7 @@ static cudaError_t enqueue_batch(DeviceBatch *B, cudaStream_t st) {
                                 (const DEntry *)B->d_entries, (const DChunk *)B->d_chunks,
                                 (const uint32_t *)B->d_order, (uint32_t)B->insts.size(), B->d_queue, B->d_scratch,
                                 B->scratch_stride, B->d_blocks, B->blocks_stride, B->d_H, B->h_stride,
-                                B->d_counters, B->smax, B->cmax);
+                                B->d_counters, B->d_stamps);
         if (ce != cudaSuccess) return ce;
     }
     else if (B->tc) LAUNCH(false, true);
@@ -1179,6 +1228,9 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
     unsigned long long hc[8] = {0};
     CUDA_TRY(cudaMemcpyAsync(hH.data(), B->d_H, sizeof(uint64_t) * hH.size(), cudaMemcpyDeviceToHost, B->stream));
     CUDA_TRY(cudaMemcpyAsync(hc, B->d_counters, sizeof(hc), cudaMemcpyDeviceToHost, B->stream));
+    std::vector<unsigned long long> hs(2 * B->insts.size() + 1);
+    CUDA_TRY(cudaMemcpyAsync(hs.data(), B->d_stamps, sizeof(unsigned long long) * hs.size(), cudaMemcpyDeviceToHost,
+                             B->stream));
     CUDA_TRY(cudaStreamSynchronize(B->stream));
     B->bytes_d2h = sizeof(uint64_t) * hH.size();
     B->ms_kernel = 0;
@@ -1200,6 +1252,9 @@ zeta_status engine_collect(DeviceEngine *e, DeviceBatch *B, std::string &err) {
         X->column_steps = X->plan.column_steps;
         X->chunks = X->plan.chunks_played;
         played += X->plan.chunks_played;
+        const unsigned long long t0 = hs[2 * B->insts.size()];
+        X->ms_dev_start = hs[2 * ii] >= t0 ? (hs[2 * ii] - t0) * 1e-6 : 0.0;
+        X->ms_dev_end = hs[2 * ii + 1] >= t0 ? (hs[2 * ii + 1] - t0) * 1e-6 : 0.0;
     }
     if (hc[2]) {
         err = "a tensor-core step timed out";

@@ -1,14 +1,20 @@
 // Learned direction policy for the reduction game (arXiv 2602.24155,
 // Sec. 3.4; Sec. 4.4 notes that the paper's policies never inspect U and
-// that better policies are open).  Inside every p-chunk (Sec. 4.1) the network
-// scores the legal directions v of each chunk and the best one is played; any
-// choice yields the same cohomology classes, only the game's cost changes.
+// that better policies are open).  The network scores the legal directions v
+// of every chunk decision the cover levels leave to a direction rule (the
+// terms whose destination is not searched, Sec. 4.1 p-chunks) and the best is
+// played; any choice yields the same cohomology classes, only the game's cost
+// changes.
 //
-// Training data comes from the game itself: the p-chunk game is played with a
-// teacher rule (the legal direction with the longest chunk, ties to the
-// smallest exponent reached), which combines more terms than Algorithm 3; every
-// chunk decision with two or more legal directions becomes a group of
-// candidates labelled with the teacher's choice.
+// Training data comes from the game itself.  The cover game is played with
+// Algorithm 3 and its chunk decisions with two or more legal directions are
+// recorded; for a sample of them (kDatasetDecisions per instance) every legal
+// direction is tried in a full rollout of the rest of the game (the same
+// cover game, Algorithm 3 elsewhere), and its cost is that plan's column steps
+// plus kChunkCost per chunk played.  The label is the cheapest direction (ties
+// to Algorithm 3's choice), and costs[row] is the row's cost above it.  The
+// network sees only local features, so it stands in for the rollouts, whose
+// cost grows with the game, in the scheduler.
 //
 // Features of a candidate (u, v), with w the exponent reached at the end of the
 // p-chunk (v first, then Algorithm 3):
@@ -19,6 +25,7 @@
 //   the p-chunk game played with Algorithm 3, as min(c, 4)/4 and [c > 0].
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -143,7 +150,9 @@ int others_at(const Instance &X, int t, const int32_t *W, uint64_t own) {
     return key == own ? c - 1 : c;
 }
 
-float mlp_score(const PolicyNet &net, const float *x) {
+}  // namespace
+
+float policy_score(const PolicyNet &net, const float *x) {
     const int F = kPolicyFeatures, H = net.hidden;
     const float *W1 = net.w, *b1 = W1 + F * H, *W2 = b1 + H, *b2 = W2 + H * H, *w3 = b2 + H, *b3 = w3 + H;
     float h1[512], h2[512];
@@ -162,33 +171,11 @@ float mlp_score(const PolicyNet &net, const float *x) {
     return out;
 }
 
-}  // namespace
+
 
 size_t policy_param_count(int hidden) {
     const size_t F = kPolicyFeatures, H = hidden;
     return F * H + H + H * H + H + H + 1;
-}
-
-bool teacher_direction(const Instance &X, const int32_t *U, int left, int *v) {
-    const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d;
-    std::vector<std::array<int, kMaxVars>> cand;
-    legal_dirs(U, nv, n, d, cand);
-    if (cand.size() < 2) return false;
-    size_t arg = 0;
-    int bestk = -1;
-    std::array<int32_t, kMaxVars> bestw{};
-    for (size_t c = 0; c < cand.size(); c++) {
-        const int k = std::min(left, kmax(U, cand[c].data(), nv, n, d));
-        std::array<int32_t, kMaxVars> w{};
-        for (int t = 0; t < nv; t++) w[t] = U[t] - k * cand[c][t];
-        if (k > bestk || (k == bestk && w < bestw)) {
-            bestk = k;
-            bestw = w;
-            arg = c;
-        }
-    }
-    for (int q = 0; q < nv; q++) v[q] = cand[arg][q];
-    return true;
 }
 
 bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int tmax, int *v) {
@@ -209,7 +196,7 @@ bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int
         p_chunk_dest(U, cand[c].data(), left, nv, n, d, W, &kf);
         float f[kPolicyFeatures];
         features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own), f);
-        float sc = mlp_score(X.net, f);
+        float sc = policy_score(X.net, f);
         if (sc > best) { best = sc; arg = c; }
     }
     for (int q = 0; q < nv; q++) v[q] = cand[arg][q];
@@ -242,63 +229,84 @@ zeta_status reference_contributions(Instance &X) {
     return ZETA_OK;
 }
 
-// Decisions of the p-chunk game played by the teacher rule (see the file comment):
-// every chunk decision with two or more legal directions, labelled with the
-// teacher's choice; costs[row] = the teacher's chunk length minus the row's
-// (0 for the label).
+// Training decisions labelled by rollouts (see the file comment).
 zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<uint32_t> &group_off,
                            std::vector<uint32_t> &labels, std::vector<int32_t> &costs) {
     if (X.nv > 4) { X.error = "the policy features cover at most four variables"; return X.status = ZETA_ERR_UNSUPPORTED; }
     if (X.Smask != (1u << X.nv) - 1) { X.error = "the learned policy takes S = {0..n} only"; return X.status = ZETA_ERR_UNSUPPORTED; }
     zeta_status st = reference_contributions(X);  // what the network sees of U
     if (st) return st;
-    X.teacher = true;
-    st = schedule_policy(X, ZETA_POLICY_PCHUNK);
-    X.teacher = false;
-    if (st) return st;
     const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p;
-    const Plan &P = X.plan;
-    const int nph = (int)P.phase_begin.size() - 1;
-    const int tmax = nph;  // phase i plays level tmax - i
-    group_off.assign(1, 0);
+    int tmax = 0;
+    for (const Chain &c : X.chains) tmax = std::max(tmax, ((norm(c.U, nv) - (int)X.base) / d + n) / p);
+    auto cost = [](const Plan &P) { return (int64_t)P.column_steps + (int64_t)kChunkCost * (int64_t)P.chunks_played; };
+    struct Dec {
+        int t, left;
+        std::array<int32_t, kMaxVars> U;
+    };
+    // 1. the cover game with Algorithm 3; its decisions (a term's first call may come from the level's search,
+    //    the second from play: both are the same decision)
+    std::vector<Dec> decs;
+    std::unordered_set<uint64_t> seen;
     std::vector<std::array<int, kMaxVars>> cand;
-    for (int ph = 0; ph < nph; ph++) {
-        const int t = tmax - ph;
-        for (uint32_t e = P.phase_begin[ph]; e < P.phase_begin[ph + 1]; e++) {
-            const PlanEntry &E = P.entries[e];
-            int32_t U[kMaxVars];
-            std::memcpy(U, E.U, sizeof(U));
-            int left = (t >= 2) ? p : p - n;
-            for (uint32_t ci = E.chunk_begin; ci < E.chunk_end; ci++) {
-                const PlanChunk &CH = P.chunks[ci];
-                legal_dirs(U, nv, n, d, cand);
-                if (cand.size() >= 2) {
-                    int32_t own_w[kMaxVars];
-                    int kf0;
-                    p_chunk_dest(U, cand[0].data(), left, nv, n, d, own_w, &kf0);
-                    const uint64_t own = pack(own_w, nv);
-                    uint32_t lab = 0;
-                    bool found = false;
-                    for (size_t c = 0; c < cand.size(); c++) {
-                        int32_t W[kMaxVars];
-                        int kf;
-                        p_chunk_dest(U, cand[c].data(), left, nv, n, d, W, &kf);
-                        float f[kPolicyFeatures];
-                        features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own), f);
-                        feat.insert(feat.end(), f, f + kPolicyFeatures);
-                        costs.push_back(CH.k - std::min(left, kmax(U, cand[c].data(), nv, n, d)));
-                        bool same = true;
-                        for (int q = 0; q < nv; q++) same &= cand[c][q] == CH.v[q];
-                        if (same) { lab = (uint32_t)c; found = true; }
-                    }
-                    if (!found) { X.error = "teacher move not among the legal directions"; return X.status = ZETA_ERR_INTERNAL; }
-                    labels.push_back(lab);
-                    group_off.push_back((uint32_t)(feat.size() / kPolicyFeatures));
-                }
-                for (int q = 0; q < nv; q++) U[q] -= CH.k * CH.v[q];
-                left -= CH.k;
+    X.hook = [&](const int32_t *U, int left, int t, int *) {
+        legal_dirs(U, nv, n, d, cand);
+        if (cand.size() >= 2) {
+            const uint64_t key = (pack(U, nv) << 12) ^ ((uint64_t)left << 6) ^ (uint64_t)t;
+            if (seen.insert(key).second) {
+                Dec D;
+                D.t = t;
+                D.left = left;
+                D.U.fill(0);
+                for (int q = 0; q < nv; q++) D.U[q] = U[q];
+                decs.push_back(D);
             }
         }
+        return false;
+    };
+    st = schedule_policy(X, ZETA_POLICY_COVER);
+    X.hook = nullptr;
+    if (st) return st;
+    const int64_t base_cost = cost(X.plan);
+    // 2. every legal direction of a sample of the decisions, each in a rollout of the whole game
+    group_off.assign(1, 0);
+    const size_t stride = std::max<size_t>(1, (decs.size() + kDatasetDecisions - 1) / kDatasetDecisions);
+    for (size_t di = 0; di < decs.size(); di += stride) {
+        const Dec &D = decs[di];
+        std::vector<std::array<int, kMaxVars>> cands;
+        legal_dirs(D.U.data(), nv, n, d, cands);
+        std::vector<int64_t> c_of(cands.size(), base_cost);
+        for (size_t c = 1; c < cands.size(); c++) {
+            X.hook = [&](const int32_t *U, int left, int t, int *v) {
+                if (t != D.t || left != D.left) return false;
+                for (int q = 0; q < nv; q++)
+                    if (U[q] != D.U[q]) return false;
+                for (int q = 0; q < nv; q++) v[q] = cands[c][q];
+                return true;
+            };
+            st = schedule_policy(X, ZETA_POLICY_COVER);
+            X.hook = nullptr;
+            if (st) return st;
+            c_of[c] = cost(X.plan);
+        }
+        size_t lab = 0;
+        for (size_t c = 1; c < cands.size(); c++)
+            if (c_of[c] < c_of[lab]) lab = c;
+        int32_t own_w[kMaxVars];
+        int kf0;
+        p_chunk_dest(D.U.data(), cands[0].data(), D.left, nv, n, d, own_w, &kf0);
+        const uint64_t own = pack(own_w, nv);
+        for (size_t c = 0; c < cands.size(); c++) {
+            int32_t W[kMaxVars];
+            int kf;
+            p_chunk_dest(D.U.data(), cands[c].data(), D.left, nv, n, d, W, &kf);
+            float f[kPolicyFeatures];
+            features(D.U.data(), cands[c].data(), W, kf, D.left, D.t, tmax, nv, d, c == 0, others_at(X, D.t, W, own), f);
+            feat.insert(feat.end(), f, f + kPolicyFeatures);
+            costs.push_back((int32_t)std::min<int64_t>(c_of[c] - c_of[lab], INT32_MAX));
+        }
+        labels.push_back((uint32_t)lab);
+        group_off.push_back((uint32_t)(feat.size() / kPolicyFeatures));
     }
     return ZETA_OK;
 }

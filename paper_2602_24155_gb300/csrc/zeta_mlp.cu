@@ -208,6 +208,16 @@ zeta_status check_hidden(uint32_t hidden) {
 
 size_t fwd_smem(int H) { return sizeof(float) * mlp_view(H).count; }
 
+// The weights staged in shared memory exceed the 48 KB default above width 110 (75.8 KB at 128): raise the
+// limit of the two kernels that stage them to what the widest network needs.
+cudaError_t mlp_kernel_attributes() {
+    const int bytes = (int)fwd_smem(kMlpMaxHidden);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)k_mlp_back_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
 }  // namespace
 
 // Forward + softmax + backward of one range of groups; grad (device) accumulated.
@@ -273,6 +283,7 @@ extern "C" zeta_status zeta_mlp_forward(zeta_ctx *ctx, uint32_t hidden, const fl
     const int H = (int)hidden;
     DevMem mem;
     float *dp, *dX, *ds;
+    MLP_TRY(mlp_kernel_attributes());
     MLP_TRY(mem.alloc(&dp, mlp_view(H).count));
     MLP_TRY(mem.alloc(&dX, n * kPolicyFeatures));
     MLP_TRY(mem.alloc(&ds, n));
@@ -299,6 +310,7 @@ extern "C" zeta_status zeta_mlp_grad(zeta_ctx *ctx, uint32_t hidden, const float
     DevMem mem;
     float *dp, *dX, *dsc, *dh1, *dh2, *dds, *dg, *dl, *dd1, *dd2;
     uint32_t *dgo, *dlab;
+    MLP_TRY(mlp_kernel_attributes());
     MLP_TRY(mem.alloc(&dd1, n * H));
     MLP_TRY(mem.alloc(&dd2, n * H));
     MLP_TRY(mem.alloc(&dp, v.count));
@@ -343,6 +355,7 @@ extern "C" zeta_status zeta_mlp_train(zeta_ctx *ctx, uint32_t hidden, float *par
     DevMem mem;
     float *dp, *dX, *dsc, *dh1, *dh2, *dds, *dg, *dm, *dv, *dl, *dd1, *dd2;
     uint32_t *dgo, *dlab;
+    MLP_TRY(mlp_kernel_attributes());
     MLP_TRY(mem.alloc(&dd1, n * H));
     MLP_TRY(mem.alloc(&dd2, n * H));
     MLP_TRY(mem.alloc(&dp, v.count));

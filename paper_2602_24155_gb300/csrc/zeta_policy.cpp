@@ -299,7 +299,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     P = Plan();
     if (X.b > 32) { X.error = "more than 32 basis columns"; return X.status = ZETA_ERR_UNSUPPORTED; }
     const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p, base = (int)X.base;
-    if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_LEARNED || X.teacher)) {
+    if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_LEARNED || X.hook)) {
         X.error = "the learned policy takes S = {0..n} only";
         return X.status = ZETA_ERR_UNSUPPORTED;
     }
@@ -428,8 +428,8 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
                 choose = [&X, t, tmax](const int32_t *U, int left, int *v) {
                     return learned_direction(X, U, left, t, tmax, v);
                 };
-            else if (X.teacher)
-                choose = [&X](const int32_t *U, int left, int *v) { return teacher_direction(X, U, left, v); };
+            else if (policy == ZETA_POLICY_COVER && X.hook)
+                choose = [&X, t](const int32_t *U, int left, int *v) { return X.hook(U, left, t, v); };
             // the learned policy plays on the cover levels: searched destinations where a term's box allows,
             // the network's directions for the others
             const bool cover = (policy == ZETA_POLICY_COVER || (policy == ZETA_POLICY_LEARNED && X.net.w)) &&

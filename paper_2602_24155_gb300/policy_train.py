@@ -1,9 +1,14 @@
 """Training of the learned direction policy (ZETA_POLICY_LEARNED).
 
-Decisions are generated by the library's own game (zeta_policy_dataset) on a
-set of training instances, concatenated in a seeded shuffled order of groups,
-and the network is trained with the library's GPU kernels (zeta_mlp_train).
+Decisions are generated by the library's own game (zeta_policy_dataset:
+rollouts of the cover game label each sampled decision with its cheapest
+direction) on a set of training instances, one host thread per instance,
+concatenated in a seeded shuffled order of groups, and the network is trained
+with the library's GPU kernels (zeta_mlp_train).
 """
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 from . import zeta_mlp_init, zeta_mlp_train, zeta_policy_dataset, POLICY_FEATURES
@@ -11,8 +16,9 @@ from . import zeta_mlp_init, zeta_mlp_train, zeta_policy_dataset, POLICY_FEATURE
 
 def build_dataset(specs, seed=0):
     Xs, offs, labs = [], [], []
-    for spec in specs:
-        X, go, lab, _ = zeta_policy_dataset(spec)
+    with ThreadPoolExecutor(max_workers=min(len(specs), os.cpu_count() or 1) or 1) as pool:
+        sets = list(pool.map(zeta_policy_dataset, specs))
+    for X, go, lab, _ in sets:
         for g in range(len(lab)):
             Xs.append(X[go[g]:go[g + 1]])
             labs.append(int(lab[g]))

@@ -63,3 +63,34 @@ def test_vector_executor_stays_within_its_register_budget():
             assert spills is None or int(spills.group(1)) == 0
             seen += 1
     assert seen == 2
+
+
+def test_int8_tensor_mma_is_not_available_on_sm_103a():
+    """The exact-integer tensor path takes fp16 digits (tcgen05.mma kind::f16) because ptxas refuses
+    kind::i8 (INT8 x INT8 -> INT32) for sm_103a; the same instruction assembles for sm_100a."""
+    import shutil
+    import subprocess
+    import tempfile
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("no nvcc")
+    src = r'''
+#include <cstdint>
+__global__ void k(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, int acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::KIND [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+'''
+    results = {}
+    with tempfile.TemporaryDirectory() as tmp:
+        for kind in ("i8", "f16"):
+            for arch in ("103a", "100a"):
+                path = os.path.join(tmp, "mma_%s.cu" % kind)
+                open(path, "w").write(src.replace("KIND", kind))
+                out = subprocess.run([nvcc, "-c", "-gencode", "arch=compute_%s,code=sm_%s" % (arch, arch), path, "-o",
+                                      os.path.join(tmp, "o.o")], capture_output=True, text=True, timeout=300)
+                results[(kind, arch)] = (out.returncode, out.stderr)
+    assert results[("i8", "103a")][0] != 0 and "not supported" in results[("i8", "103a")][1]
+    assert results[("i8", "100a")][0] == 0
+    assert results[("f16", "103a")][0] == 0

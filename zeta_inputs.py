@@ -153,6 +153,23 @@ def draw_instance(workload, i, accept, max_attempts=100000):
     raise RuntimeError("no accepted candidate for %s[%d]" % (workload, i))
 
 
+# The mixed stream: 64 instances of uneven size for one persistent launch (curves, surfaces, threefolds), as
+# (workload, index) pairs of the workloads above, plus diagonal forms ("fermat", (n, d, p)).  The paper's cubic
+# fourfolds (s = 3003) are not among them: the library refuses s > 512.
+MIXED_STREAM = ([("quartic_curve_f11", 0)] + [("quintic_curves", i) for i in range(24)] +
+                [("cubic_surfaces", i) for i in range(16)] + [("quartic_k3", i) for i in range(21)] +
+                [("fermat", (4, 3, 7)), ("fermat", (4, 3, 13))])
+
+
+def draw_mixed(k, accept):
+    """Instance k of MIXED_STREAM as (n, d, p, coeffs)."""
+    workload, x = MIXED_STREAM[k]
+    if workload == "fermat":
+        n, d, p = x
+        return n, d, p, fermat(n, d)
+    return draw_instance(workload, x, accept)[:4]
+
+
 def random_residues(seed, count, modulus):
     """`count` residues uniform in [0, modulus) (kernel-level parity inputs)."""
     st = Stream(seed, 0xABCDEF, count)
