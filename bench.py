@@ -332,7 +332,7 @@ def _cubic_survey(z, ctx, stream, torch):
     count = zi.WORKLOADS["cubic_surfaces"]["count"]
     specs = [zi.draw_instance("cubic_surfaces", i, accept)[:4] for i in range(count)]
     s = 84
-    alu_peak = 152 * 64 / 6 * 2070.0 * 1e6 / 1e12      # the main line's ALU peak at the maximum SM clock
+    alu_peak = 152 * 64 * 2070.0 * 1e6 / 1e12      # mad.wide.u32 at the maximum SM clock, as the main line
 
     def timed(policy):
         plan = z.zeta_batch_prepare(ctx, specs, policy=policy)
@@ -348,11 +348,13 @@ def _cubic_survey(z, ctx, stream, torch):
         plan.release()
         ms = e0.elapsed_time(e1)
         ok = sum(1 for x in per if x["status"] == 0)
-        achieved = tot["column_steps"] * s * s / (ms / 1000.0) / 1e12
+        # every modulus here is below 2^56: four mad.wide.u32 per modular multiply-add
+        achieved = 4 * tot["column_steps"] * s * s / (ms / 1000.0) / 1e12
         return P, {"policy": policy, "ms_per_launch": ms, "zeta_per_s": count / (ms / 1000.0), "launches": 1,
                    "column_steps": tot["column_steps"], "completed": "%d/%d" % (ok, count),
                    "ms_host_setup": tot["ms_host_setup"],
-                   "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
+                   "modmac_per_s": tot["column_steps"] * s * s / (ms / 1000.0),
+                   "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T mad.wide.u32/s",
                                 "frac": achieved / alu_peak}}
     P, line = timed("p_chunk")
     out = {"workload": "cubic_surfaces_%d" % count, "primes": [7, 11, 13], "S": [3], "s": s, "b": 6}
@@ -540,11 +542,13 @@ def main():
                                                         and chosen == "vector") else None
     ms_kernel = tot["ms_kernel"] / max(1, tot["kernel_launches"])
     macs_per_launch = tot["column_steps"] * s * s
-    achieved = macs_per_launch / (ms_kernel / 1000.0) / 1e12
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    # ALU peak of the implemented arithmetic: 152 SMs x 64 mad.wide.u32 per SM per clock
-    # (a probe measured 59-63) / 6 mad.wide.u32 per modular multiply-add (20 x 30-bit limbs)
-    alu_peak = 152 * 64 / 6 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # mad.wide.u32 per launch as the executor computes them: four per modular multiply-add when q = p^M < 2^56
+    # (28-bit limbs), six otherwise (20-bit x 30-bit limbs)
+    madw_per_launch = sum(st["column_steps"] * st["s"] ** 2 * (4 if sp[2] ** st["M"] < (1 << 56) else 6)
+                          for sp, st in zip(specs, per))
+    achieved = madw_per_launch / (ms_kernel / 1000.0) / 1e12
+    # ALU peak: 152 SMs x 64 mad.wide.u32 per SM per clock (nominal) at the maximum SM clock
+    alu_peak = 152 * 64 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "zeta/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -560,10 +564,13 @@ def main():
         "policies": policies,
         "paths": paths,
         "autotune": tuning,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tmodmac/s",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "T mad.wide.u32/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "k_execute", "ms_per_launch": ms_kernel,
-                     "peak_basis": ("152 SM x 64 mad.wide.u32/clk / 6 per modular MAC (20x30-bit limbs) at %.0f MHz"
+                     "modmac_per_s": macs_per_launch / (ms_kernel / 1000.0),
+                     "madw_per_launch": madw_per_launch,
+                     "peak_basis": ("152 SM x 64 mad.wide.u32/clk (nominal) at %.0f MHz; achieved counts 4 per "
+                                    "modular multiply-add for q < 2^56 (28-bit limbs), 6 above (20 x 30-bit limbs)"
                                     % peaks.get("sm_max_mhz", 2070.0))
                                    + ("" if chosen == "vector" else "; tensor-core path: its CUDA-core epilogue "
                                       "(digit fold and reduction) bounds it, the tensor pipe is the minor share")},
