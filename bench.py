@@ -222,7 +222,7 @@ def _k3_survey(z, ctx, stream, torch):
             "column_steps": tot["column_steps"], "heights": dict(sorted(hist.items()))}
 
 
-def _k3_full(z, ctx, stream, torch, count):
+def _k3_full(z, ctx, stream, torch, count, N=0):
     """Quartic K3 surfaces (n = 3, d = 4: s = 220, b = 21) over F_7, F_11, F_13 (every tenth sparse) at the full
     precision of the library's rules, the first `count` of the 512-surface workload in one persistent launch on
     thread-block clusters (each cluster reduces one surface; its CTAs hold row slices of the step matrices)."""
@@ -237,7 +237,8 @@ def _k3_full(z, ctx, stream, torch, count):
             raise
     specs = [zi.draw_instance("quartic_k3", i, accept)[:4] for i in range(count)]
     t0 = time.perf_counter()
-    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk")
+    # N > 0: every series order truncated to N (a small case for profiling; P(T) is then not the zeta function)
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", **(dict(N=N, r=4, y_only=True) if N else {}))
     setup_s = time.perf_counter() - t0
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -260,8 +261,10 @@ def _k3_full(z, ctx, stream, torch, count):
     madw = 4 * tot["column_steps"] * s * s
     peak = 152 * 64 * 2070.0 * 1e6 / 1e12
     achieved = madw / (ms / 1000.0) / 1e12
-    return {"workload": "quartic_k3_%d of 512" % count, "primes": [7, 11, 13], "precision": "full (r_m, N_m of the "
-            "library's rules; exact P(T) of degree 21)", "s": s, "b": 21, "ms_per_launch": ms,
+    return {"workload": "quartic_k3_%d of 512" % count, "primes": [7, 11, 13],
+            "precision": ("full (r_m, N_m of the library's rules; exact P(T) of degree 21)" if not N else
+                          "truncated: N_m = %d, r = 4, unnormalised columns only (profiling case)" % N),
+            "s": s, "b": 21, "ms_per_launch": ms,
             "zeta_per_s": count / (ms / 1000.0), "launches": 1, "completed": "%d/%d" % (ok, count),
             "column_steps": tot["column_steps"], "column_steps_per_s": tot["column_steps"] / (ms / 1000.0),
             "modmac_per_s": tot["column_steps"] * s * s / (ms / 1000.0), "host_setup_s": setup_s,
@@ -387,6 +390,8 @@ def main():
     ap.add_argument("--no-k3", action="store_true", help="skip the K3 height survey (512 surfaces, precision 1)")
     ap.add_argument("--k3-count", type=int, default=76,
                     help="quartic K3 surfaces of the 512-surface workload run at full precision (0: skip)")
+    ap.add_argument("--k3-N", type=int, default=0,
+                    help="truncate the K3 line's series orders to N (small profiling case; 0 = full precision)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed stream")
     ap.add_argument("--no-cubic", action="store_true",
                     help="skip the cubic-surface line (1024 surfaces, S = {3}, full precision)")
@@ -582,7 +587,7 @@ def main():
         line["k3_heights"] = _k3_survey(z, ctx, stream, torch)
     if rank == 0 and world == 1 and args.k3_count > 0:
         try:
-            line["k3_full"] = _k3_full(z, ctx, stream, torch, args.k3_count)
+            line["k3_full"] = _k3_full(z, ctx, stream, torch, args.k3_count, args.k3_N)
         except Exception as exc:   # reported, never a reason to lose the main line
             line["k3_full"] = {"error": repr(exc)[:200]}
     if rank == 0 and world == 1 and not args.no_mixed:

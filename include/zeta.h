@@ -142,10 +142,12 @@ typedef struct {
     uint64_t bytes_h2d;      /* bytes copied host -> device (start terms, sections, tables) */
     uint64_t bytes_d2h;      /* bytes copied device -> host (numerators) */
     /* Device latency of the instance inside its persistent launch (batches;
-     * per instance only): the times, in ms after the launch's first block
-     * started, at which a block (or cluster) took the instance from the queue
-     * and at which its numerators were written back.  The instance's result
-     * is complete on the device at ms_dev_end. */
+     * per instance only): the times, in ms after the launch's first cluster
+     * started, at which a cluster took the instance from the queue and at
+     * which its numerators were written back; the instance's result is
+     * complete on the device at ms_dev_end.  Recorded by the cluster executor,
+     * which runs every batch holding an instance with s > 128 (all of the
+     * batch's instances); batches of smaller instances report 0 for both. */
     double ms_dev_start;
     double ms_dev_end;
 } zeta_stats;
