@@ -30,9 +30,10 @@ import zeta_inputs as zi  # noqa: E402
 METRIC = "exact zeta funcs/s + reduction steps/s mod p^N on 1 GB300; learned vs plain policy"
 
 # DRAM bytes (read + written) per instance of the executor k_execute on the quintic-curve workload under the
-# learned policy, from one ncu capture of the current kernels on a small case (the capture command and its
-# scaling to a full launch are recorded with the profiles); None when no capture of these kernels exists.
-DRAM_BYTES_PER_INSTANCE = None
+# learned policy: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of the current kernels on 456
+# instances of the workload (bench.py --count 456 --path vector), scaled by the instance count; traffic grows in
+# proportion to the instances (the merge blocks and inputs of each are written and read once).
+DRAM_BYTES_PER_INSTANCE = (2.312358e9 + 2.177106e9) / 456
 WORKLOAD = "quintic_curves"
 
 
