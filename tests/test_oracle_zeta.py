@@ -173,3 +173,15 @@ def test_hasse_witt_against_brute_force_counts():
     a = pins.counts_to_charpoly_prefix(2, 7, counts)
     hw = pins.hasse_witt_charpoly_mod_p(2, 4, 7, c)
     assert [x % 7 for x in a] == hw
+
+
+def test_fermat_quintic_surface_over_f11_is_ordinary():
+    # the paper's statement (Sec. 6, quintic surfaces) that x^5 + y^5 + z^5 + w^5 is ordinary at 11, from Weil's
+    # Gauss-sum formula: degree 52, every reciprocal root of absolute value 11, Newton polygon = Hodge polygon
+    # (slopes 0, 1, 2 with multiplicities 4, 44, 4)
+    from oracle.precision import hodge_polygon, vp
+    P = pins.fermat_charpoly(3, 5, 11, dps=200)
+    assert len(P) == 53 and P[0] == 1
+    assert pins.root_moduli_ok(3, 11, P, dps=200)
+    H = hodge_polygon(3, [1] * 4 + [2] * 44 + [3] * 4)
+    assert all(P[i] != 0 and vp(P[i], 11) == H[i] for i in range(1, 53))
