@@ -198,12 +198,13 @@ zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta
                           int64_t *P_out, zeta_stats *st);
 
 /* Many hypersurfaces (any mix of n, d, p; with opt->S_mask = 0 each takes its
- * own default S, so curves and cubic surfaces share a launch).  Batches of
- * 256 or more are split
- * into four sub-batches (eight from 2048) whose host setup overlaps the device
- * work of the previous one; consecutive sub-batches alternate between the
- * context's stream and a second stream of the context, so that their
- * persistent launches overlap.
+ * own default S, so curves, surfaces and threefolds share a launch).  Batches
+ * of 256 or more are split into two sub-batches (four from 512, eight from
+ * 2048), heaviest
+ * instances first (estimated from the precision alone), whose host setup
+ * overlaps the device work of the previous one; consecutive sub-batches
+ * alternate between the context's stream and a second stream of the context,
+ * so that their persistent launches overlap.  Outputs are in input order.
  *  P_out: count * stride * 2 int64; instance i writes b_i+1 coefficients
  *         (two words each, as in zeta_charpoly) at P_out + 2*i*stride
  *         (stride >= max b_i + 1).

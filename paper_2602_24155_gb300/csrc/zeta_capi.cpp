@@ -305,13 +305,36 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
     // Pipelined: the host setup of sub-batch i+1 runs while the GPU reduces
     // sub-batch i (launches are asynchronous), and consecutive sub-batches
     // alternate between two streams so that the next persistent launch fills
-    // the SMs the previous one's tail leaves idle.
-    const size_t S = count >= 2048 ? 8 : count >= 256 ? 4 : 1;
+    // the SMs the previous one's tail leaves idle.  Instances are taken
+    // heaviest first (estimated from the precision alone: p x sum_m N_m x the
+    // limb products per multiply-add), so that the longest instances start in
+    // the first launch and the lighter ones fill the tails (4096 plane quintics
+    // end to end on a GB300: 5.03 s in eight sub-batches of the input order,
+    // 4.98 s in one, 3.83 s in eight heaviest-first).  Results go back in the
+    // caller's order.
+    const size_t S = count >= 2048 ? 8 : count >= 512 ? 4 : count >= 256 ? 2 : 1;
+    std::vector<double> key(count, 0.0);
+    zeta_options o = opt ? *opt : default_options();
+    if (S > 1)
+        parallel_for(count, ctx->threads, [&](size_t i) {
+            Instance X;
+            if (prepare_instance(&hs[i], &o, false, X) != ZETA_OK) return;
+            uint32_t nsum = 0;
+            for (uint32_t m = 0; m < X.n; m++) nsum += X.N[m];
+            key[i] = (double)X.p * nsum * (X.q < ((uint64_t)1 << 56) ? 4.0 : 6.0);
+        });
+    std::vector<size_t> order(count);
+    for (size_t i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return key[x] > key[y]; });
+    std::vector<zeta_hypersurface> hp(count);
+    for (size_t i = 0; i < count; i++) hp[i] = hs[order[i]];
+    std::vector<int64_t> Pp(2 * count * std::max<size_t>(stride, 1), 0);
+    std::vector<zeta_stats> statp(per_instance ? count : 0);
     std::vector<zeta_batch_plan *> plans(S, nullptr);
     zeta_status st = ZETA_OK;
     for (size_t i = 0; i < S && !st; i++) {
         const size_t a = count * i / S, b = count * (i + 1) / S;
-        st = batch_prepare_lane(ctx, hs + a, b - a, opt, (int)(i & 1), &plans[i]);
+        st = batch_prepare_lane(ctx, hp.data() + a, b - a, opt, (int)(i & 1), &plans[i]);
         if (!st) st = zeta_batch_run(ctx, plans[i]);
     }
     zeta_stats agg;
@@ -319,8 +342,8 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
     for (size_t i = 0; i < S && !st; i++) {
         const size_t a = count * i / S, b = count * (i + 1) / S;
         zeta_stats part;
-        st = zeta_batch_finish(ctx, plans[i], P_out + 2 * a * stride, stride, per_instance ? per_instance + a : nullptr,
-                               &part);
+        st = zeta_batch_finish(ctx, plans[i], Pp.data() + 2 * a * stride, stride,
+                               per_instance ? statp.data() + a : nullptr, &part);
         if (st) break;
         agg.chains += part.chains;
         agg.terms += part.terms;
@@ -335,7 +358,12 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
         agg.bytes_d2h += part.bytes_d2h;
     }
     for (auto *P : plans) zeta_batch_release(P);
-    if (!st && total) *total = agg;
+    if (st) return st;
+    for (size_t i = 0; i < count; i++) {
+        std::memcpy(P_out + 2 * order[i] * stride, Pp.data() + 2 * i * stride, sizeof(int64_t) * 2 * stride);
+        if (per_instance) per_instance[order[i]] = statp[i];
+    }
+    if (total) *total = agg;
     return st;
 }
 
