@@ -421,7 +421,7 @@ def main():
         from paper_2602_24155_gb300.policy_train import train_policy
         train = _instances_range(world * args.count, args.train_count, z)
         t0 = time.perf_counter()
-        weights, train_loss, decisions = train_policy(ctx, train, hidden=8, epochs=30)
+        weights, train_loss, decisions = train_policy(ctx, train, hidden=8, epochs=60)
         learned = {"train_s": time.perf_counter() - t0, "decisions": decisions, "loss": train_loss,
                    "hidden": 8, "train_instances": len(train)}
         opt.update(weights=weights, hidden=8)

@@ -336,7 +336,7 @@ zeta_status zeta_horner_static(void *cuda_stream, uint32_t count, uint32_t s, ui
  * is the mean over groups of -log softmax(scores of the group)[label].
  * Buffers are host buffers owned by the caller.
  * ------------------------------------------------------------------------- */
-#define ZETA_POLICY_FEATURES 17
+#define ZETA_POLICY_FEATURES 18
 
 /* Number of floats of the parameter vector for hidden width H. */
 size_t zeta_mlp_param_count(uint32_t hidden);

@@ -8,7 +8,7 @@ finite differences in the tests.
 """
 import numpy as np
 
-F = 17
+F = 18
 
 
 def unpack(params, H):

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libzeta.so")
 
 POLICY = {"p_chunk": 0, "depth_first": 1, "var_by_var": 2, "learned": 3, "cover": 4}
-POLICY_FEATURES = 17
+POLICY_FEATURES = 18
 PATH = {"vector": 0, "gemm": 1, "auto": 2}
 PATH_NAME = {v: k for k, v in PATH.items()}
 

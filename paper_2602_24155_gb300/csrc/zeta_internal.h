@@ -1,6 +1,7 @@
 // Internal interfaces between the host setup (zeta_host.cpp) and the CUDA
 // kernels (zeta_kernels.cu).  Not part of the public ABI.
 #pragma once
+#include <array>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -62,7 +63,7 @@ struct Plan {
 };
 
 // Learned direction policy (zeta_learn.cpp).
-constexpr int kPolicyFeatures = 17;
+constexpr int kPolicyFeatures = 18;
 struct PolicyNet {
     const float *w = nullptr;  // W1 (F x H), b1 (H), W2 (H x H), b2 (H), w3 (H), b3 (1)
     int hidden = 0;
@@ -96,8 +97,12 @@ struct Instance {
     std::vector<int32_t> tab_secrow;  // nv x s: row (i, omega - 1_S + e_i) of sec, or -1
     Plan plan;
     PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
-    // per level t: exponent -> terms reaching it in the p-chunk game with Algorithm 3
+    // per level t: exponent -> terms reaching it in the reference game (the cover game with Algorithm 3), and
+    // for each basis column the number of those terms that carry it
     std::vector<std::unordered_map<uint64_t, int>> ref_contrib;
+    std::vector<std::unordered_map<uint64_t, std::array<uint16_t, 32>>> ref_cols;
+    // columns carried by the term whose chunk direction is being chosen (set by the scheduler before it asks)
+    mutable uint32_t cur_live = 0;
     // ZETA_POLICY_COVER with a decision hook: the hook chooses the direction of every chunk decision
     // (U, steps left in the p-chunk, level t); false = Algorithm 3 (training-data rollouts)
     std::function<bool(const int32_t *U, int left, int t, int *v)> hook;
@@ -133,7 +138,8 @@ zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<ui
                            std::vector<uint32_t> &labels, std::vector<int32_t> &costs);
 // Host copy of the network's forward pass, used by the scheduler (zeta_mlp_forward_host).
 float policy_score(const PolicyNet &net, const float *x);
-// Plays the p-chunk game with Algorithm 3 and records, per level, how many terms reach each exponent.
+// Plays the reference game (the cover game with Algorithm 3) and records, per level, how many terms reach each
+// exponent and which columns they carry.
 zeta_status reference_contributions(Instance &X);
 zeta_status finish_y_only(Instance &X);  // Y = Fin * H only
 

@@ -22,7 +22,8 @@
 //   k/left (this chunk's length over the steps left), t/tmax (level),
 //   [v is Algorithm 3's choice],
 //   and what the policy sees of U: the number c of other terms that reach w in
-//   the p-chunk game played with Algorithm 3, as min(c, 4)/4 and [c > 0].
+//   the reference game (the cover game with Algorithm 3), as min(c, 4)/4 and
+//   [c > 0], and the share of the term's columns those terms carry to w.
 #include <algorithm>
 #include <array>
 #include <climits>
@@ -126,7 +127,7 @@ void p_chunk_dest(const int32_t *U, const int *v, int left, int nv, int n, int d
 }
 
 void features(const int32_t *U, const int *v, const int32_t *W, int k_first, int left, int t, int tmax, int nv, int d,
-              bool is_greedy, int others, float *f) {
+              bool is_greedy, int others, float overlap, float *f) {
     const float nu = (float)std::max(1, norm(U, nv)), nw = (float)std::max(1, norm(W, nv));
     for (int i = 0; i < 4; i++) {
         f[i] = i < nv ? U[i] / nu : 0.f;
@@ -138,6 +139,7 @@ void features(const int32_t *U, const int *v, const int32_t *W, int k_first, int
     f[14] = is_greedy ? 1.f : 0.f;
     f[15] = (float)std::min(std::max(others, 0), 4) / 4.f;
     f[16] = others > 0 ? 1.f : 0.f;
+    f[17] = overlap;
 }
 
 // Other terms of the reference game that reach W at level t - 1, for the term at U
@@ -148,6 +150,19 @@ int others_at(const Instance &X, int t, const int32_t *W, uint64_t own) {
     auto it = X.ref_contrib[t - 1].find(key);
     int c = it == X.ref_contrib[t - 1].end() ? 0 : it->second;
     return key == own ? c - 1 : c;
+}
+
+// Share of the term's columns (live) that other terms of the reference game carry to W at level t - 1: the
+// columns a merge there would save (the term's own contribution is not counted when W is its own destination).
+float overlap_at(const Instance &X, int t, const int32_t *W, uint64_t own, uint32_t live) {
+    if (!live || t - 1 < 1 || t - 1 >= (int)X.ref_cols.size()) return 0.f;
+    const uint64_t key = pack(W, (int)X.nv);
+    auto it = X.ref_cols[t - 1].find(key);
+    if (it == X.ref_cols[t - 1].end()) return 0.f;
+    int shared = 0;
+    for (int col = 0; col < 32; col++)
+        if ((live >> col & 1u) && (int)it->second[col] - (key == own ? 1 : 0) > 0) shared++;
+    return (float)shared / (float)__builtin_popcount(live);
 }
 
 }  // namespace
@@ -195,7 +210,8 @@ bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int
         int kf;
         p_chunk_dest(U, cand[c].data(), left, nv, n, d, W, &kf);
         float f[kPolicyFeatures];
-        features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own), f);
+        features(U, cand[c].data(), W, kf, left, t, tmax, nv, d, c == 0, others_at(X, t, W, own),
+                 overlap_at(X, t, W, own, X.cur_live), f);
         float sc = policy_score(X.net, f);
         if (sc > best) { best = sc; arg = c; }
     }
@@ -204,27 +220,43 @@ bool learned_direction(const Instance &X, const int32_t *U, int left, int t, int
 }
 
 zeta_status reference_contributions(Instance &X) {
-    zeta_status st = schedule_policy(X, ZETA_POLICY_PCHUNK);
+    // the game the network plays in, with Algorithm 3 for every choice it would make
+    std::function<bool(const int32_t *, int, int, int *)> saved = X.hook;
+    X.hook = nullptr;
+    zeta_status st = schedule_policy(X, ZETA_POLICY_COVER);
+    X.hook = saved;
     if (st) return st;
     const int nv = (int)X.nv;
     const Plan &P = X.plan;
     const int nph = (int)P.phase_begin.size() - 1;
     const int tmax = nph;  // phase i plays level tmax - i
     X.ref_contrib.assign(tmax + 1, {});
+    X.ref_cols.assign(tmax + 1, {});
+    auto add = [&](int t, uint64_t key, uint32_t live) {
+        X.ref_contrib[t][key] += 1;
+        auto &cnt = X.ref_cols[t][key];
+        for (int col = 0; col < 32; col++)
+            if (live >> col & 1u) cnt[col]++;
+    };
     for (int ph = 0; ph + 1 < nph; ph++) {
         const int tn = tmax - ph - 1;  // next level
         std::vector<uint64_t> block_key;
         for (uint32_t e = P.phase_begin[ph + 1]; e < P.phase_begin[ph + 2]; e++) {
             const PlanEntry &E = P.entries[e];
             const uint64_t key = pack(E.U, nv);
-            if (E.start_chain >= 0) X.ref_contrib[tn][key] += 1;
+            if (E.start_chain >= 0) {
+                const Chain &C = X.chains[E.start_chain];
+                uint32_t live = 0;
+                for (uint32_t t = C.term_begin; t < C.term_end; t++) live |= 1u << X.terms[t].col;
+                add(tn, key, live);
+            }
             if (E.arrival >= 0) {
                 if ((int)block_key.size() <= E.arrival) block_key.resize(E.arrival + 1, 0);
                 block_key[E.arrival] = key;
             }
         }
         for (uint32_t e = P.phase_begin[ph]; e < P.phase_begin[ph + 1]; e++)
-            if (P.entries[e].dest >= 0) X.ref_contrib[tn][block_key[P.entries[e].dest]] += 1;
+            if (P.entries[e].dest >= 0) add(tn, block_key[P.entries[e].dest], P.entries[e].live);
     }
     return ZETA_OK;
 }
@@ -242,6 +274,7 @@ zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<ui
     auto cost = [](const Plan &P) { return (int64_t)P.column_steps + (int64_t)kChunkCost * (int64_t)P.chunks_played; };
     struct Dec {
         int t, left;
+        uint32_t live;
         std::array<int32_t, kMaxVars> U;
     };
     // 1. the cover game with Algorithm 3; its decisions (a term's first call may come from the level's search,
@@ -257,6 +290,7 @@ zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<ui
                 Dec D;
                 D.t = t;
                 D.left = left;
+                D.live = X.cur_live;
                 D.U.fill(0);
                 for (int q = 0; q < nv; q++) D.U[q] = U[q];
                 decs.push_back(D);
@@ -301,7 +335,8 @@ zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<ui
             int kf;
             p_chunk_dest(D.U.data(), cands[c].data(), D.left, nv, n, d, W, &kf);
             float f[kPolicyFeatures];
-            features(D.U.data(), cands[c].data(), W, kf, D.left, D.t, tmax, nv, d, c == 0, others_at(X, D.t, W, own), f);
+            features(D.U.data(), cands[c].data(), W, kf, D.left, D.t, tmax, nv, d, c == 0, others_at(X, D.t, W, own),
+                     overlap_at(X, D.t, W, own, D.live), f);
             feat.insert(feat.end(), f, f + kPolicyFeatures);
             costs.push_back((int32_t)std::min<int64_t>(c_of[c] - c_of[lab], INT32_MAX));
         }

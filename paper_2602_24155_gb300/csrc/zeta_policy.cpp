@@ -80,6 +80,7 @@ void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_step
                  const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
     const int nv = (int)X.nv, base = (int)X.base, d = (int)X.d;
     int left = max_steps;
+    X.cur_live = live;
     while (norm(U, nv) > base && left > 0 && !stop(U)) {
         int v[kMaxVars];
         if (!(choose && choose(U, left, v))) greedy_v(U, nv, d, v, X.Smask);
@@ -205,6 +206,7 @@ std::vector<std::vector<int32_t>> cover_destinations(
             int leftsteps = L;
             while (leftsteps > 0 && norm(u.data(), nv) > (int)X.base) {
                 int v[kMaxVars];  // the direction the level will play (the same chooser as play_chunks)
+                X.cur_live = P.entries[e0 + i].live;
                 if (!(choose && choose(u.data(), leftsteps, v))) greedy_v(u.data(), nv, d, v, X.Smask);
                 const int k = std::min(k_max(u.data(), v, nv, (int)X.base, d), leftsteps);
                 if (k <= 0) break;
