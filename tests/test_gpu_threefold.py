@@ -59,3 +59,29 @@ def test_dense_cubic_threefold_f11_equals_the_oracle(threefolds):
     assert P[1] == P_ref
     assert pins.charpoly_to_counts(n, p, P[1], 1) == [pins.count_points(n, d, p, c, 1)]
     assert pins.root_moduli_ok(n, p, P[1])
+
+
+def test_newton_strata_search_over_cubic_threefolds():
+    """The paper's Method 1 (Sec. 5.1) over cubic threefolds: random dense cubics over F_11, the slope-one length
+    (the p-rank analogue of Sec. 1.2) from a relative-precision-1 batch, then full precision for the non-ordinary
+    ones (length <= 4), whose P(T) must satisfy #X(F_11), Weil and the filter's own count."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2602_24155_gb300.newton import first_slope_length, search
+    ctx = z.zeta_create(0, torch.cuda.current_stream().cuda_stream)
+    try:
+        out = search(ctx, 4, 3, 11, 80, seed=2)
+    finally:
+        z.zeta_destroy(ctx)
+    print("cubic threefolds over F_11:", {k: v for k, v in out.items() if k != "strata"},
+          {lab: len(v) for lab, v in out["strata"].items()})
+    assert out["smooth"] >= 8          # about one in six random cubics is smooth and {4}-smooth over F_11
+    assert sum(out["p_rank"].values()) == out["smooth"]
+    assert set(out["p_rank"]) <= set(range(6))
+    assert out["kept"] == sum(len(v) for v in out["strata"].values())
+    for items in out["strata"].values():
+        for coeffs, P in items:
+            assert len(P) == 11 and P[0] == 1
+            assert pins.root_moduli_ok(4, 11, P)
+            assert pins.charpoly_to_counts(4, 11, P, 1) == [pins.count_points(4, 3, 11, coeffs, 1)]
+            assert first_slope_length(P, 11, 1) <= 4
