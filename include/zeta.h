@@ -120,6 +120,13 @@ typedef struct {
 /* Stop after the unnormalised columns Y (no division by p^(v-m+1), no
  * charpoly): for truncated precisions whose Y is not divisible. */
 #define ZETA_FLAG_Y_ONLY 1u
+/* Where the setup's right inverses over Z/q are solved (the section of
+ * Prop. 3.3 and the final reduction's levels, Sec. 3.3 step (2); Gauss-Jordan
+ * with unit pivots, the same matrices either way).  Neither flag: on the
+ * device for batches holding an instance with C(dn, n) > 128, on the host
+ * otherwise.  Batch calls only (zeta_batch_prepare, zeta_batch). */
+#define ZETA_FLAG_HOST_SETUP 2u
+#define ZETA_FLAG_DEVICE_SETUP 4u
 
 typedef struct {
     int32_t status;          /* per-instance status (zeta_batch) */
@@ -430,6 +437,18 @@ typedef struct {
 zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta_plan_info *info,
                       uint64_t *sec, int32_t *chain_U, uint32_t *chain_terms, uint32_t *term_rc,
                       uint64_t *term_coeff, uint64_t *fin);
+
+/* zeta_plan's sec and fin with the setup's right inverses solved on the
+ * device (k_right_inverse: one block per matrix, [A | I] in device memory,
+ * Gauss-Jordan over Z/q with unit pivots in column order, the first unit row
+ * as pivot; Prop. 3.3 proof, Sec. 3.3 step (2)) and the rest of the setup on
+ * the host.  Equal to zeta_plan's word for word: exact arithmetic with the
+ * same pivot rule.  sec, fin: host buffers sized as zeta_plan's (either may
+ * be NULL); ms_device: the solve kernel's time (CUDA events), may be NULL.
+ * ZETA_ERR_UNSUPPORTED when a matrix's C + R words exceed a block's shared
+ * memory (about 29 000). */
+zeta_status zeta_plan_device(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, uint64_t *sec,
+                             uint64_t *fin, double *ms_device);
 
 /* The index tables the device's step-matrix generation reads for one
  * instance (host only).  The kernel forms, for output row r and input

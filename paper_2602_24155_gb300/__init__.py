@@ -31,8 +31,11 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
            "zeta_batch_release", "zeta_horner_device", "zeta_horner_static", "zeta_plan", "zeta_finish",
            "zeta_mlp_param_count", "zeta_mlp_init", "zeta_mlp_forward", "zeta_mlp_grad", "zeta_mlp_train",
            "zeta_policy_dataset", "zeta_autotune", "zeta_selftest_wait", "zeta_plan_moves",
-           "zeta_plan_tables", "zeta_mlp_forward_host"]
+           "zeta_plan_tables", "zeta_mlp_forward_host", "zeta_plan_device"]
 FLAG_Y_ONLY = 1
+FLAG_HOST_SETUP = 2
+FLAG_DEVICE_SETUP = 4
+SETUP = {"auto": 0, "host": FLAG_HOST_SETUP, "device": FLAG_DEVICE_SETUP}
 
 
 class ZetaError(RuntimeError):
@@ -140,6 +143,8 @@ def _load():
                                       P(Stats), P(Stats)]
     lib.zeta_batch_release.argtypes = [ctypes.c_void_p]
     lib.zeta_plan_tables.argtypes = [P(Hypersurface), P(Options), ctypes.c_void_p, ctypes.c_void_p]
+    lib.zeta_plan_device.argtypes = [ctypes.c_void_p, P(Hypersurface), P(Options), ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double)]
     lib.zeta_plan_moves.argtypes = [P(Hypersurface), P(Options), P(ctypes.c_size_t), P(ctypes.c_size_t),
                                     P(ctypes.c_size_t), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.zeta_selftest_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)]
@@ -166,13 +171,14 @@ LIB = _Lazy()
 
 
 def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0,
-             block_threads=0, S=None):
+             block_threads=0, S=None, setup="auto"):
     """S: the index set of Prop. 3.3 as variable indices (None = the library's choice: {0..n} when
-    d >= n + 1, else {n})."""
+    d >= n + 1, else {n}).  setup: where batch calls solve the setup's right inverses ("auto",
+    "host" or "device")."""
     o = Options()
     o.block_threads = block_threads
     o.S_mask = sum(1 << int(i) for i in set(S)) if S else 0
-    o.flags = FLAG_Y_ONLY if y_only else 0
+    o.flags = (FLAG_Y_ONLY if y_only else 0) | SETUP[setup]
     if weights is not None:
         w = np.ascontiguousarray(weights, dtype=np.float32)
         o.policy_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
@@ -389,6 +395,22 @@ def zeta_plan(spec, **opt):
                 sec=sec, U=U, chain_terms=ct, term_rc=rc, term_coeff=co, fin=fin,
                 game=dict(chunks=info.plan_chunks, steps=info.plan_steps, column_steps=info.plan_column_steps,
                           merges=info.plan_merges, entries=info.plan_entries, cap=info.plan_cap))
+
+
+def zeta_plan_device(ctx, spec, **opt):
+    """zeta_plan's section and final reduction map with the right inverses solved on the device.
+    Returns (sec, fin, kernel ms)."""
+    hs = _hypersurface(spec)
+    o = _options(**opt)
+    info = PlanInfo()
+    _check(None, LIB.zeta_plan(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(info), None, None, None,
+                               None, None, None))
+    sec = np.zeros((info.sec_rows, info.sec_cols), dtype=np.uint64)
+    fin = np.zeros((info.b, info.h_rows), dtype=np.uint64)
+    ms = ctypes.c_double(0)
+    _check(ctx, LIB.zeta_plan_device(ctx, ctypes.byref(hs), ctypes.byref(o), sec.ctypes.data, fin.ctypes.data,
+                                     ctypes.byref(ms)))
+    return sec, fin, ms.value
 
 
 def zeta_finish(spec, H, **opt):

@@ -198,7 +198,49 @@ extern "C" {
 
 // zeta_batch_prepare on a given lane of the engine (0: the context's stream, 1: the engine's second stream).
 static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
-                                      int lane, zeta_batch_plan **out);
+                                      int lane, zeta_batch_plan **out, Instance *begun = nullptr);
+
+// C(dn, n), the side of the step matrices (0 when out of range).
+static uint64_t step_side(uint32_t n, uint32_t d) {
+    if (n < 1 || n > 16 || d < 2 || d > 64) return 0;
+    uint64_t r = 1;
+    for (uint32_t i = 1; i <= n; i++) r = r * (uint64_t)(d * n - n + i) / i;
+    return r;
+}
+
+// The setup's right inverses go to the device for batches holding an instance with s > 128 (there
+// the host's Gauss-Jordan is most of the setup: about 2 s for a cubic threefold), unless a flag
+// chooses; plane curves keep them on the host, whose setup is hidden behind the previous launch.
+static bool wants_device_setup(const zeta_options &o, const zeta_hypersurface *hs, size_t count) {
+    if (o.flags & ZETA_FLAG_HOST_SETUP) return false;
+    if (o.flags & ZETA_FLAG_DEVICE_SETUP) return true;
+    for (size_t i = 0; i < count; i++)
+        if (step_side(hs[i].n, hs[i].d) > 128) return true;
+    return false;
+}
+
+// Host setup of X[0..count) up to the right inverses (in parallel), then the right inverses of all
+// of them in one device launch.  prepare_complete finishes each instance.
+static zeta_status begin_on_device(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options &o,
+                                   Instance *X, double *ms_solve) {
+    parallel_for(count, ctx->threads, [&](size_t i) {
+        X[i].net.w = o.policy_weights;
+        X[i].net.hidden = (int)o.policy_hidden;
+        prepare_instance(&hs[i], &o, true, X[i], true);
+    });
+    std::vector<SolveJob *> jobs;
+    std::vector<uint64_t> qs, ps;
+    for (size_t i = 0; i < count; i++) {
+        if (X[i].status != ZETA_OK || !X[i].solves_pending) continue;
+        for (SolveJob &J : X[i].solves)
+            if (J.R) {
+                jobs.push_back(&J);
+                qs.push_back(X[i].q);
+                ps.push_back(X[i].p);
+            }
+    }
+    return engine_solve(ctx->engine, jobs, qs, ps, ctx->error, ms_solve);
+}
 
 extern "C" {
 
@@ -210,7 +252,7 @@ zeta_status zeta_batch_prepare(zeta_ctx *ctx, const zeta_hypersurface *hs, size_
 }  // extern "C"
 
 static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count, const zeta_options *opt,
-                                      int lane, zeta_batch_plan **out) {
+                                      int lane, zeta_batch_plan **out, Instance *begun) {
     if (!ctx || !out || (!hs && count)) return ZETA_ERR_ARG;
     *out = nullptr;
     zeta_batch_plan *P = new (std::nothrow) zeta_batch_plan();
@@ -218,10 +260,23 @@ static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs
     P->opt = opt ? *opt : default_options();
     P->inst.resize(count);
     double t0 = now_ms();
+    const bool device = !begun && wants_device_setup(P->opt, hs, count);
+    if (begun) {
+        for (size_t i = 0; i < count; i++) P->inst[i] = std::move(begun[i]);
+    } else if (device) {
+        zeta_status st = begin_on_device(ctx, hs, count, P->opt, P->inst.data(), nullptr);
+        if (st) { delete P; return st; }
+    }
     parallel_for(count, ctx->threads, [&](size_t i) {
-        P->inst[i].net.w = P->opt.policy_weights;
-        P->inst[i].net.hidden = (int)P->opt.policy_hidden;
-        if (prepare_instance(&hs[i], &P->opt, true, P->inst[i]) == ZETA_OK) schedule_policy(P->inst[i], P->opt.policy);
+        Instance &X = P->inst[i];
+        if (!begun && !device) {
+            X.net.w = P->opt.policy_weights;
+            X.net.hidden = (int)P->opt.policy_hidden;
+            if (prepare_instance(&hs[i], &P->opt, true, X) != ZETA_OK) return;
+        } else if (X.status != ZETA_OK || (X.solves_pending && prepare_complete(X) != ZETA_OK)) {
+            return;
+        }
+        schedule_policy(X, P->opt.policy);
     });
     for (auto &X : P->inst)
         if (X.status == ZETA_OK) P->ok.push_back(&X);
@@ -332,9 +387,17 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
     std::vector<zeta_stats> statp(per_instance ? count : 0);
     std::vector<zeta_batch_plan *> plans(S, nullptr);
     zeta_status st = ZETA_OK;
+    // device-solved setups are begun for every sub-batch before the first launch: a solve queued
+    // behind a running persistent launch would wait for it
+    std::vector<Instance> begun;
+    if (S > 1 && wants_device_setup(o, hp.data(), count)) {
+        begun.resize(count);
+        st = begin_on_device(ctx, hp.data(), count, o, begun.data(), nullptr);
+    }
     for (size_t i = 0; i < S && !st; i++) {
         const size_t a = count * i / S, b = count * (i + 1) / S;
-        st = batch_prepare_lane(ctx, hp.data() + a, b - a, opt, (int)(i & 1), &plans[i]);
+        st = batch_prepare_lane(ctx, hp.data() + a, b - a, opt, (int)(i & 1), &plans[i],
+                                begun.empty() ? nullptr : begun.data() + a);
         if (!st) st = zeta_batch_run(ctx, plans[i]);
     }
     zeta_stats agg;
@@ -474,6 +537,32 @@ zeta_status zeta_plan(const zeta_hypersurface *hs, const zeta_options *opt, zeta
         if (term_rc) { term_rc[2 * t] = X.terms[t].row; term_rc[2 * t + 1] = X.terms[t].col; }
         if (term_coeff) term_coeff[t] = X.terms[t].coeff;
     }
+    if (fin) std::memcpy(fin, X.fin.data(), sizeof(uint64_t) * X.fin.size());
+    return ZETA_OK;
+}
+
+zeta_status zeta_plan_device(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, uint64_t *sec,
+                             uint64_t *fin, double *ms_device) {
+    if (!ctx || !hs) return ZETA_ERR_ARG;
+    if (ms_device) *ms_device = 0;
+    if (!ctx->engine) { ctx->error = "no device engine"; return ZETA_ERR_DEVICE; }
+    zeta_options o = opt ? *opt : default_options();
+    Instance X;
+    zeta_status st = prepare_instance(hs, &o, true, X, true);
+    if (st) { ctx->error = X.error; return st; }
+    std::vector<SolveJob *> jobs;
+    std::vector<uint64_t> qs, ps;
+    for (SolveJob &J : X.solves)
+        if (J.R) {
+            jobs.push_back(&J);
+            qs.push_back(X.q);
+            ps.push_back(X.p);
+        }
+    if ((st = engine_solve(ctx->engine, jobs, qs, ps, ctx->error, ms_device))) return st;
+    for (SolveJob *J : jobs)
+        if (!J->done) { ctx->error = "a right inverse is too wide for the device solve"; return ZETA_ERR_UNSUPPORTED; }
+    if ((st = prepare_complete(X))) { ctx->error = X.error; return st; }
+    if (sec) std::memcpy(sec, X.sec.data(), sizeof(uint64_t) * X.sec.size());
     if (fin) std::memcpy(fin, X.fin.data(), sizeof(uint64_t) * X.fin.size());
     return ZETA_OK;
 }

@@ -388,8 +388,11 @@ static inline uint64_t pack_u(const int *U, int nv) {
     return key;
 }
 
+static void build_solves(const Setup &S, Instance &X);
+static zeta_status complete_reduction(const Setup &S, Instance &X, double t0);
+
 zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *opt, bool build_reduction,
-                             Instance &X) {
+                             Instance &X, bool defer_solves) {
     double t0 = now_ms();
     if (!hs || !hs->coeffs) { X.error = "null hypersurface"; return X.status = ZETA_ERR_ARG; }
     uint32_t n = hs->n, d = hs->d, p = hs->p;
@@ -417,7 +420,14 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     setup_poly(S, hs);
     if (!smooth(S)) { X.error = "f is not smooth (Jacobian criterion)"; return X.status = ZETA_ERR_NOT_SMOOTH; }
     X.kappa = (n + 1) * (d - 1) + 1 - Ssize;
-    if (Smask != full && !s_smooth(S, Smask, (int)X.kappa)) {
+    // deferred: the section's rank decides (the unit-pivot elimination over Z/q reaches full rank iff
+    // the map is onto mod p), unless an earlier error is returned first
+    X.s_smooth_deferred = defer_solves && build_reduction && Smask != full;
+    auto not_s_smooth = [&]() {
+        if (!s_smooth(S, Smask, (int)X.kappa)) { X.error = "f is not S-smooth (Definition 3.1)"; return true; }
+        return false;
+    };
+    if (Smask != full && !X.s_smooth_deferred && !s_smooth(S, Smask, (int)X.kappa)) {
         X.error = "f is not S-smooth (Definition 3.1)";
         return X.status = ZETA_ERR_NOT_SMOOTH;
     }
@@ -449,37 +459,119 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     X.M = (uint32_t)Mp;
     // the device keeps residues mod q as two 30-bit limbs (vector path) or at most
     // eight balanced base-256 digits (tensor-core path): q < 2^60
-    if (!pow_fits(p, X.M, (uint64_t)1 << 60, &X.q)) { X.error = "p^M exceeds 2^60"; return X.status = ZETA_ERR_PRECISION; }
+    if (!pow_fits(p, X.M, (uint64_t)1 << 60, &X.q)) {
+        if (X.s_smooth_deferred && not_s_smooth()) return X.status = ZETA_ERR_NOT_SMOOTH;
+        X.error = "p^M exceeds 2^60";
+        return X.status = ZETA_ERR_PRECISION;
+    }
     for (uint32_t m = 1; m <= n; m++) {
         uint64_t tmp;
-        if (X.N[m - 1] && !pow_fits(p, X.N[m - 1] + m - 1, (uint64_t)1 << 63, &tmp)) { X.error = "p^s exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
+        if (X.N[m - 1] && !pow_fits(p, X.N[m - 1] + m - 1, (uint64_t)1 << 63, &tmp)) {
+            if (X.s_smooth_deferred && not_s_smooth()) return X.status = ZETA_ERR_NOT_SMOOTH;
+            X.error = "p^s exceeds 2^63";
+            return X.status = ZETA_ERR_PRECISION;
+        }
     }
     if (!build_reduction) { X.ms_setup = now_ms() - t0; return ZETA_OK; }
 
-    const uint64_t q = X.q;
-    Mont mq(q);
-    const int nv = X.nv;
+    build_solves(S, X);
+    if (defer_solves) {
+        X.solves_pending = true;
+        X.ms_setup = now_ms() - t0;
+        return ZETA_OK;
+    }
+    return complete_reduction(S, X, t0);
+}
 
-    // Section: right inverse of the map of J_S in degree kappa (Prop. 3.3 proof),
-    // Sec[(i,nu), gamma] = coefficient of x^nu in G_i, sum_i G_i d_i f = x^gamma.
-    // Columns (i, nu) outside J_S stay zero, so Gauss-Jordan never pivots there
-    // and their rows of Sec are zero; for S = {0..n} every column is in.
+// The right inverses' matrices (Montgomery form): [0] the section of the map of J_S in degree
+// kappa (Prop. 3.3 proof), Sec[(i,nu), gamma] = coefficient of x^nu in G_i, sum_i G_i d_i f =
+// x^gamma; columns (i, nu) outside J_S stay zero, so Gauss-Jordan never pivots there and their
+// rows of Sec are zero (for S = {0..n} every column is in).  [m], m = 1..n: the final reduction
+// at pole order m (Sec. 3.3 step (2)), rows Homog_k, k = dm - n - 1, columns the basis elements
+// of pole order m and then the map (i, nu) -> x^nu d_i f from Homog_{k-d+1}; empty when k < 0.
+static void build_solves(const Setup &S, Instance &X) {
+    const Mont mq(X.q);
+    const int n = (int)X.n, d = (int)X.d;
+    const uint32_t Smask = X.Smask;
+    X.solves.assign(n + 1, SolveJob());
     {
         Monos rows, src;
         std::vector<std::vector<std::pair<int, uint32_t>>> cols;
         jacobian_columns(S, X.kappa, rows, src, cols);
-        int R = rows.count, C = (int)cols.size();
-        std::vector<uint64_t> A((size_t)R * C, 0);
-        for (int c = 0; c < C; c++) {
+        SolveJob &J = X.solves[0];
+        J.R = rows.count;
+        J.C = (int)cols.size();
+        J.A.assign((size_t)J.R * J.C, 0);
+        for (int c = 0; c < J.C; c++) {
             if (!in_JS(Smask, c / src.count, src.at(c % src.count))) continue;
-            for (auto &pr : cols[c]) A[(size_t)pr.first * C + c] = mq.add(A[(size_t)pr.first * C + c], mq.to(pr.second));
+            for (auto &pr : cols[c])
+                J.A[(size_t)pr.first * J.C + c] = mq.add(J.A[(size_t)pr.first * J.C + c], mq.to(pr.second));
         }
-        std::vector<uint64_t> Xinv;
-        if (!right_inverse(R, C, A, mq, p, Xinv)) { X.error = "section: Jacobian map not onto"; return X.status = ZETA_ERR_INTERNAL; }
+    }
+    for (int m = 1; m <= n; m++) {
+        const int k = d * m - n - 1;
+        Monos rows = monomials(S.nv, k);
+        if (rows.count == 0) continue;
+        std::vector<int> bset;
+        for (uint32_t t = 0; t < X.b; t++)
+            if (X.pole[t] == (uint32_t)m) bset.push_back((int)t);
+        std::vector<std::vector<std::pair<int, uint32_t>>> jcols;
+        Monos r2, src;
+        if (k - d + 1 >= 0) jacobian_columns(S, k, r2, src, jcols);
+        SolveJob &J = X.solves[m];
+        J.R = rows.count;
+        J.C = (int)bset.size() + (int)jcols.size();
+        J.A.assign((size_t)J.R * J.C, 0);
+        for (size_t c = 0; c < bset.size(); c++)
+            J.A[(size_t)mono_rank(X.basis_exp[bset[c]].data(), S.nv, k) * J.C + c] = mq.one;
+        const size_t nb = bset.size();
+        for (size_t c = 0; c < jcols.size(); c++)
+            for (auto &pr : jcols[c])
+                J.A[(size_t)pr.first * J.C + nb + c] = mq.add(J.A[(size_t)pr.first * J.C + nb + c], mq.to(pr.second));
+    }
+}
+
+zeta_status prepare_complete(Instance &X) {
+    if (!X.solves_pending) { X.error = "prepare_complete without a deferred prepare_instance"; return X.status = ZETA_ERR_INTERNAL; }
+    const double t0 = now_ms() - X.ms_setup;
+    zeta_hypersurface hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.n = X.n;
+    hs.d = X.d;
+    hs.p = X.p;
+    hs.coeffs = X.coeffs.data();
+    Setup S;
+    setup_poly(S, &hs);
+    X.solves_pending = false;
+    return complete_reduction(S, X, t0);
+}
+
+// Everything after the right inverses: the section and the step-matrix tables, the final
+// reduction map, the Frobenius expansion.  Solves the jobs still open on the host.
+static zeta_status complete_reduction(const Setup &S, Instance &X, double t0) {
+    const uint32_t n = X.n, d = X.d, p = X.p;
+    const uint32_t Smask = X.Smask;
+    const uint64_t q = X.q;
+    Mont mq(q);
+    const int nv = X.nv;
+    for (SolveJob &J : X.solves)
+        if (J.R && !J.done) {
+            J.ok = right_inverse(J.R, J.C, J.A, mq, p, J.X);
+            J.done = true;
+        }
+    {
+        SolveJob &J = X.solves[0];
+        if (!J.ok) {
+            if (X.s_smooth_deferred) { X.error = "f is not S-smooth (Definition 3.1)"; return X.status = ZETA_ERR_NOT_SMOOTH; }
+            X.error = "section: Jacobian map not onto";
+            return X.status = ZETA_ERR_INTERNAL;
+        }
+        const int R = J.R, C = J.C;
+        const Monos src = monomials(nv, (int)X.kappa - (int)d + 1);
         X.sec_rows = C;
         X.sec_cols = R;
         X.sec.resize((size_t)C * R);
-        for (size_t t = 0; t < X.sec.size(); t++) X.sec[t] = mq.from(Xinv[t]);
+        for (size_t t = 0; t < X.sec.size(); t++) X.sec[t] = mq.from(J.X[t]);
 
         // index tables of the device's step-matrix generation: with e = mu + 1 - 1_S the
         // S = {0..n} formulas R[omega, mu] = sum_i (u_i + e_omega,i) Sec[(i, e_omega - 1 + e_i),
@@ -503,7 +595,6 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
 
     // Final reduction map (Sec. 3.3 step (2)): Fin[beta, h], h in Homog_{dn-n-1}.
     {
-        std::vector<int> bidx(X.b);
         struct Level { Monos rows; int nb; std::vector<int> bcols; Monos src; std::vector<uint64_t> Xinv; int ncols; };
         std::vector<Level> lev(n + 1);
         for (uint32_t m = 1; m <= n; m++) {
@@ -516,18 +607,11 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
                 if (X.pole[t] == m) bset.push_back((int)t);
             L.nb = (int)bset.size();
             L.bcols = bset;
-            std::vector<std::vector<std::pair<int, uint32_t>>> jcols;
-            Monos r2;
-            if (k - (int)d + 1 >= 0) jacobian_columns(S, k, r2, L.src, jcols);
-            int C = L.nb + (int)jcols.size(), R = L.rows.count;
-            L.ncols = C;
-            std::vector<uint64_t> A((size_t)R * C, 0);
-            for (int c = 0; c < L.nb; c++)
-                A[(size_t)mono_rank(X.basis_exp[bset[c]].data(), nv, k) * C + c] = mq.one;
-            for (size_t c = 0; c < jcols.size(); c++)
-                for (auto &pr : jcols[c])
-                    A[(size_t)pr.first * C + L.nb + c] = mq.add(A[(size_t)pr.first * C + L.nb + c], mq.to(pr.second));
-            if (!right_inverse(R, C, A, mq, p, L.Xinv)) { X.error = "final reduction: not onto"; return X.status = ZETA_ERR_INTERNAL; }
+            if (k - (int)d + 1 >= 0) L.src = monomials(nv, k - (int)d + 1);
+            L.ncols = L.nb + nv * L.src.count;
+            SolveJob &J = X.solves[m];
+            if (!J.ok || J.R != L.rows.count || J.C != L.ncols) { X.error = "final reduction: not onto"; return X.status = ZETA_ERR_INTERNAL; }
+            L.Xinv.swap(J.X);
         }
         X.fin.assign((size_t)X.b * X.h_rows, 0);
         std::vector<uint64_t> inv_m(n + 1, 0);
@@ -673,6 +757,7 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
             X.chains.push_back(ch);
         }
     }
+    std::vector<SolveJob>().swap(X.solves);
     X.ms_setup = now_ms() - t0;
     return ZETA_OK;
 }

@@ -69,6 +69,17 @@ struct PolicyNet {
     int hidden = 0;
 };
 
+// One right inverse over Z/q (Prop. 3.3 section; the final reduction's levels, Sec. 3.3 step (2)):
+// A (R x C, full row rank mod p) in, X (C x R, A X = I) out, both in Montgomery form (R = 2^64).
+// Solved on the host (right_inverse) or on the device (engine_solve); both run Gauss-Jordan
+// with unit pivots, columns in order, the first unit row as pivot, so both give the same X.
+struct SolveJob {
+    int R = 0, C = 0;
+    std::vector<uint64_t> A;
+    std::vector<uint64_t> X;
+    bool done = false, ok = false;
+};
+
 struct Instance {
     // input
     uint32_t n = 0, d = 0, p = 0, nv = 0;
@@ -95,6 +106,10 @@ struct Instance {
     // index tables of the device's step-matrix generation (zeta_plan_tables)
     std::vector<int32_t> tab_monoS;   // s x nv: mu + 1 - 1_S
     std::vector<int32_t> tab_secrow;  // nv x s: row (i, omega - 1_S + e_i) of sec, or -1
+    // right inverses of the reduction build: [0] the section, [m] the final reduction at pole order m
+    std::vector<SolveJob> solves;
+    bool solves_pending = false;      // prepare_instance stopped before using them (prepare_complete resumes)
+    bool s_smooth_deferred = false;   // the S-smoothness test is the section's rank (ZETA_ERR_NOT_SMOOTH if short)
     Plan plan;
     PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
     // per level t: exponent -> terms reaching it in the reference game (the cover game with Algorithm 3), and
@@ -120,8 +135,12 @@ struct Instance {
 };
 
 // Host-side steps (zeta_host.cpp)
+// defer_solves: stop once the right inverses' matrices are built (X.solves, X.solves_pending), so that
+// they can be solved together on the device; prepare_complete solves what is left on the host and
+// finishes the reduction data.  The S-smoothness test is then read from the section's rank.
 zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *opt,
-                             bool build_reduction, Instance &X);
+                             bool build_reduction, Instance &X, bool defer_solves = false);
+zeta_status prepare_complete(Instance &X);
 zeta_status finish_instance(Instance &X);
 // Plays the policy on the start chains of X and fills X.plan (zeta_policy.cpp).
 zeta_status validate_plan(Instance &X);
@@ -169,5 +188,9 @@ void engine_batch_timing(const DeviceBatch *B, double *ms_kernel, uint64_t *laun
 zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint32_t s, uint32_t c,
                           const uint32_t *k, const uint64_t *A, const uint64_t *B, uint64_t *W,
                           const uint64_t *q, std::string &err);
+// Solves the jobs on the device (zeta_setup.cuh), each modulo qs[t] with unit test mod ps[t];
+// sets done, ok (full row rank) and X.  Jobs too wide for the kernel's shared memory are left undone.
+zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, const std::vector<uint64_t> &qs,
+                         const std::vector<uint64_t> &ps, std::string &err, double *ms_device);
 
 }  // namespace zeta

@@ -580,6 +580,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
 
 }  // namespace zeta
 #include "zeta_cluster.cuh"
+#include "zeta_setup.cuh"
 namespace zeta {
 
 // Kernel-level Algorithm 2 on independent problems (zeta_horner_device):
@@ -1347,6 +1348,110 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
     return ZETA_OK;
 }
 
+
+// Right inverses of the host setup on the device (k_right_inverse, one block per job).  A job whose
+// pivot row (C + R words) does not fit the block's shared memory is left for the host.
+zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, const std::vector<uint64_t> &qs,
+                         const std::vector<uint64_t> &ps, std::string &err, double *ms_device) {
+    if (ms_device) *ms_device = 0;
+    if (jobs.size() != qs.size() || jobs.size() != ps.size()) { err = "engine_solve: sizes differ"; return ZETA_ERR_ARG; }
+    CUDA_TRY(cudaSetDevice(e->device));
+    int max_smem = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, e->device));
+    std::vector<SolveDesc> descs;
+    std::vector<SolveJob *> mine;
+    std::vector<uint32_t> nz_idx;
+    std::vector<uint64_t> nz_val;
+    uint64_t work = 0, outw = 0;
+    uint32_t npiv = 0, maxW = 0;
+    for (size_t t = 0; t < jobs.size(); t++) {
+        SolveJob &J = *jobs[t];
+        if (J.done || J.R <= 0 || J.C <= 0) continue;
+        const uint64_t W = (uint64_t)J.C + (uint64_t)J.R;
+        if (W * sizeof(uint64_t) > (uint64_t)max_smem || (uint64_t)J.R * (uint64_t)J.C >= ((uint64_t)1 << 32)) continue;
+        if (J.A.size() != (size_t)J.R * J.C || qs[t] < 3 || !(qs[t] & 1) || qs[t] >= ((uint64_t)1 << 60) || ps[t] < 2) {
+            err = "engine_solve: malformed job";
+            return ZETA_ERR_ARG;
+        }
+        SolveDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.Q = make_modq(qs[t]);
+        d.p = ps[t];
+        d.aug = work;
+        d.out = outw;
+        d.nz = nz_idx.size();
+        for (size_t x = 0; x < J.A.size(); x++)
+            if (J.A[x]) {
+                nz_idx.push_back((uint32_t)x);
+                nz_val.push_back(J.A[x]);
+            }
+        d.nnz = (uint32_t)(nz_idx.size() - d.nz);
+        d.R = (uint32_t)J.R;
+        d.C = (uint32_t)J.C;
+        d.W = (uint32_t)W;
+        d.piv = npiv;
+        work += (uint64_t)J.R * W;
+        outw += (uint64_t)J.R * J.R;
+        npiv += (uint32_t)J.R;
+        maxW = std::max(maxW, (uint32_t)W);
+        descs.push_back(d);
+        mine.push_back(&J);
+    }
+    if (descs.empty()) return ZETA_OK;
+    const uint32_t count = (uint32_t)descs.size();
+    SolveDesc *d_desc;
+    uint32_t *d_idx;
+    uint64_t *d_val, *d_work, *d_out;
+    int32_t *d_piv, *d_rank;
+    zeta_status st;
+    if ((st = upload(e, "sv_desc", descs, &d_desc, err))) return st;
+    if ((st = upload(e, "sv_idx", nz_idx, &d_idx, err))) return st;
+    if ((st = upload(e, "sv_val", nz_val, &d_val, err))) return st;
+    if ((st = ensure(e, "sv_work", sizeof(uint64_t) * work, (void **)&d_work, err))) return st;
+    if ((st = ensure(e, "sv_out", sizeof(uint64_t) * outw, (void **)&d_out, err))) return st;
+    if ((st = ensure(e, "sv_piv", sizeof(int32_t) * npiv, (void **)&d_piv, err))) return st;
+    if ((st = ensure(e, "sv_rank", sizeof(int32_t) * count, (void **)&d_rank, err))) return st;
+    const size_t smem = (size_t)maxW * sizeof(uint64_t);
+    CUDA_TRY(cudaFuncSetAttribute((const void *)k_right_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_right_inverse, kSolveThreads, smem));
+    const int grid = (int)std::min<uint64_t>(count, (uint64_t)e->sms * std::max(per_sm, 1));
+    cudaEvent_t ev[2];
+    CUDA_TRY(cudaEventCreate(&ev[0]));
+    CUDA_TRY(cudaEventCreate(&ev[1]));
+    cudaEventRecord(ev[0], e->stream);
+    k_right_inverse<<<grid, kSolveThreads, smem, e->stream>>>(d_desc, count, d_idx, d_val, d_work, d_out, d_piv, d_rank);
+    cudaError_t le = cudaGetLastError();
+    cudaEventRecord(ev[1], e->stream);
+    std::vector<uint64_t> out(outw);
+    std::vector<int32_t> piv(npiv), rank(count);
+    if (le == cudaSuccess) {
+        le = cudaMemcpyAsync(out.data(), d_out, sizeof(uint64_t) * outw, cudaMemcpyDeviceToHost, e->stream);
+        if (le == cudaSuccess) le = cudaMemcpyAsync(piv.data(), d_piv, sizeof(int32_t) * npiv, cudaMemcpyDeviceToHost, e->stream);
+        if (le == cudaSuccess) le = cudaMemcpyAsync(rank.data(), d_rank, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, e->stream);
+        if (le == cudaSuccess) le = cudaStreamSynchronize(e->stream);
+    }
+    float ms = 0;
+    if (le == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    CUDA_TRY(le);
+    if (ms_device) *ms_device = ms;
+    for (uint32_t t = 0; t < count; t++) {
+        SolveJob &J = *mine[t];
+        const SolveDesc &d = descs[t];
+        const int R = J.R, r = rank[t];
+        J.X.assign((size_t)J.C * R, 0);
+        for (int k = 0; k < r && k < R; k++) {
+            const int c = piv[d.piv + k];
+            if (c < 0 || c >= J.C) { err = "engine_solve: pivot column out of range"; return ZETA_ERR_INTERNAL; }
+            std::memcpy(&J.X[(size_t)c * R], &out[d.out + (size_t)k * R], sizeof(uint64_t) * R);
+        }
+        J.ok = r == R;
+        J.done = true;
+    }
+    return ZETA_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the kernel-level entry point (zeta_horner_static).
