@@ -127,6 +127,11 @@ typedef struct {
  * otherwise.  Batch calls only (zeta_batch_prepare, zeta_batch). */
 #define ZETA_FLAG_HOST_SETUP 2u
 #define ZETA_FLAG_DEVICE_SETUP 4u
+/* Run every instance of a batch on the whole-GPU executor (one instance at
+ * a time, every kernel over all SMs; step matrices in device memory), which
+ * instances with C(dn, n) > 512 (cubic fourfolds: 3003) always take, after the
+ * batch's persistent launch.  Needs q = p^M < 2^56 and C(dn, n) <= 4096. */
+#define ZETA_FLAG_WHOLE_GPU 8u
 
 typedef struct {
     int32_t status;          /* per-instance status (zeta_batch) */

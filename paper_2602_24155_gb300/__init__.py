@@ -35,6 +35,7 @@ EXPORTS = ["zeta_create", "zeta_destroy", "zeta_last_error", "zeta_query", "zeta
 FLAG_Y_ONLY = 1
 FLAG_HOST_SETUP = 2
 FLAG_DEVICE_SETUP = 4
+FLAG_WHOLE_GPU = 8
 SETUP = {"auto": 0, "host": FLAG_HOST_SETUP, "device": FLAG_DEVICE_SETUP}
 
 
@@ -171,14 +172,15 @@ LIB = _Lazy()
 
 
 def _options(policy="depth_first", path="vector", r=0, N=None, y_only=False, weights=None, hidden=0,
-             block_threads=0, S=None, setup="auto"):
+             block_threads=0, S=None, setup="auto", whole_gpu=False):
     """S: the index set of Prop. 3.3 as variable indices (None = the library's choice: {0..n} when
     d >= n + 1, else {n}).  setup: where batch calls solve the setup's right inverses ("auto",
-    "host" or "device")."""
+    "host" or "device").  whole_gpu: run every instance on the whole-GPU executor (instances with
+    C(dn, n) > 512 always are)."""
     o = Options()
     o.block_threads = block_threads
     o.S_mask = sum(1 << int(i) for i in set(S)) if S else 0
-    o.flags = (FLAG_Y_ONLY if y_only else 0) | SETUP[setup]
+    o.flags = (FLAG_Y_ONLY if y_only else 0) | SETUP[setup] | (FLAG_WHOLE_GPU if whole_gpu else 0)
     if weights is not None:
         w = np.ascontiguousarray(weights, dtype=np.float32)
         o.policy_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))

@@ -186,11 +186,28 @@ zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta
 struct zeta_batch_plan {
     std::vector<Instance> inst;
     std::vector<Instance *> ok;
+    std::vector<Instance *> large;  // run one at a time on the whole-GPU executor (s > 512, or ZETA_FLAG_WHOLE_GPU)
     zeta_options opt;
     DeviceBatch *dev = nullptr;
-    double ms_setup = 0, ms_device = 0;
-    bool launched = false;
+    double ms_setup = 0, ms_device = 0, ms_large = 0;
+    uint64_t large_launches = 0;
+    bool launched = false, large_done = false;
 };
+
+// The instances of the whole-GPU executor, in plan order, after the persistent launch was enqueued.
+static zeta_status run_large(zeta_ctx *ctx, zeta_batch_plan *P) {
+    if (P->large_done) return ZETA_OK;
+    P->large_done = true;
+    for (Instance *X : P->large) {
+        double ms = 0;
+        uint64_t launches = 0;
+        zeta_status st = engine_run_large(ctx->engine, *X, ctx->error, &ms, &launches);
+        if (st) return st;
+        P->ms_large += ms;
+        P->large_launches += launches;
+    }
+    return ZETA_OK;
+}
 
 extern "C" {
 
@@ -282,9 +299,13 @@ static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs
         if (X.status == ZETA_OK) P->ok.push_back(&X);
         else if (ctx->error.empty()) ctx->error = X.error;
     P->ms_setup = now_ms() - t0;
-    if (!P->ok.empty()) {
-        resolve_path(ctx, P->ok, P->opt);
-        zeta_status st = engine_prepare(ctx->engine, P->ok, P->opt.policy, P->opt.path, P->opt.block_threads, lane,
+    std::vector<Instance *> small;
+    for (Instance *X : P->ok)
+        if (X->s > 512 || (P->opt.flags & ZETA_FLAG_WHOLE_GPU)) P->large.push_back(X);
+        else small.push_back(X);
+    if (!small.empty()) {
+        resolve_path(ctx, small, P->opt);
+        zeta_status st = engine_prepare(ctx->engine, small, P->opt.policy, P->opt.path, P->opt.block_threads, lane,
                                         &P->dev, ctx->error);
         if (st) { delete P; return st; }
     }
@@ -296,9 +317,12 @@ extern "C" {
 
 zeta_status zeta_batch_run(zeta_ctx *ctx, zeta_batch_plan *P) {
     if (!ctx || !P) return ZETA_ERR_ARG;
-    if (!P->dev) return ZETA_OK;
-    P->launched = true;
-    return engine_launch(ctx->engine, P->dev, ctx->error);
+    if (P->dev && !P->launched) {
+        P->launched = true;
+        zeta_status st = engine_launch(ctx->engine, P->dev, ctx->error);
+        if (st) return st;
+    }
+    return run_large(ctx, P);
 }
 
 zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *P, int64_t *P_out, size_t stride,
@@ -306,11 +330,16 @@ zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *P, int64_t *P_out,
     if (!ctx || !P || (!P_out && !P->inst.empty())) return ZETA_ERR_ARG;
     for (Instance *X : P->ok)
         if ((size_t)X->b + 1 > stride) return ZETA_ERR_ARG;
+    if (P->dev && !P->launched) {
+        P->launched = true;
+        zeta_status st = engine_launch(ctx->engine, P->dev, ctx->error);
+        if (st) return st;
+    }
+    {
+        zeta_status st = run_large(ctx, P);
+        if (st) return st;
+    }
     if (P->dev) {
-        if (!P->launched) {
-            zeta_status st = engine_launch(ctx->engine, P->dev, ctx->error);
-            if (st) return st;
-        }
         zeta_status st = engine_collect(ctx->engine, P->dev, ctx->error);
         if (st) return st;
     }
@@ -343,6 +372,8 @@ zeta_status zeta_batch_finish(zeta_ctx *ctx, zeta_batch_plan *P, int64_t *P_out,
     agg.ms_host_setup = P->ms_setup;
     agg.ms_host_finish = t3 - t2;
     engine_batch_timing(P->dev, &agg.ms_kernel, &agg.kernel_launches, &agg.bytes_h2d, &agg.bytes_d2h);
+    agg.ms_kernel += P->ms_large;
+    agg.kernel_launches += P->large_launches;
     if (total) *total = agg;
     return ZETA_OK;
 }

@@ -273,20 +273,60 @@ static bool smooth(const Setup &S) {
 // for i not in S only the multiples of x_i d_i f, i.e. nu_i >= 1.
 static bool in_JS(uint32_t Smask, int i, const int *nu) { return ((Smask >> i) & 1u) || nu[i] >= 1; }
 
-// S-smooth iff the map of J_S is onto Homog_kappa mod p, kappa = (n+1)(d-1)+1-|S|:
-// the n+1 generators of J_S (|S| of degree d-1, the others of degree d) have no
-// common zero iff they form a regular sequence, iff they span every form of the
-// degree one above the socle of their quotient (Macaulay).
-static bool s_smooth(const Setup &S, uint32_t Smask, int kappa) {
-    Monos rows, src;
-    std::vector<std::vector<std::pair<int, uint32_t>>> cols;
-    jacobian_columns(S, kappa, rows, src, cols);
-    std::vector<uint32_t> A((size_t)cols.size() * rows.count, 0);
-    for (size_t c = 0; c < cols.size(); c++) {
-        if (!in_JS(Smask, (int)(c / src.count), src.at((int)(c % src.count)))) continue;
-        for (auto &pr : cols[c]) A[c * rows.count + pr.first] = (A[c * rows.count + pr.first] + pr.second) % S.p;
+// n' forms of degree e in n' variables (coefficients mod p over Homog_e of those variables) have no common zero
+// over the algebraic closure iff they span every form of degree n'(e-1)+1: with no common zero they are a regular
+// sequence, whose quotient vanishes above its socle degree n'(e-1) (Macaulay); with one it vanishes in no degree.
+static bool no_common_zero(int nv, int e, const std::vector<std::vector<uint32_t>> &forms, uint32_t p) {
+    const int D = nv * (e - 1) + 1;
+    const Monos rows = monomials(nv, D), src = monomials(nv, D - e), me = monomials(nv, e);
+    const int ncols = nv * src.count;
+    std::vector<uint32_t> A((size_t)ncols * rows.count, 0);
+    std::vector<int> g(nv);
+    for (int i = 0; i < nv; i++)
+        for (int a = 0; a < src.count; a++) {
+            const size_t c = (size_t)i * src.count + a;
+            for (int t = 0; t < me.count; t++) {
+                const uint32_t v = forms[i][t] % p;
+                if (!v) continue;
+                for (int z = 0; z < nv; z++) g[z] = me.at(t)[z] + src.at(a)[z];
+                uint32_t &x = A[c * rows.count + mono_rank(g.data(), nv, D)];
+                x = (x + v) % p;
+            }
+        }
+    return (int)pivot_columns_mod_p(ncols, rows.count, A, p).size() == rows.count;
+}
+
+// S-smooth (Definition 3.1): d_i f for i in S and x_i d_i f for i not in S have no common zero.  A common zero x
+// with Z = {i not in S : x_i = 0} is a common zero of the n+1-|Z| forms d_i f, i not in Z, restricted to the
+// coordinate subspace {x_i = 0, i in Z}; conversely every such zero is one of J_S.  So f is S-smooth iff, for every
+// Z within the complement of S, those restricted forms (a square system) have no common zero; Z = {} is the
+// Jacobian criterion, tested before.  The largest of these eliminations has |Homog_{(n+1)(d-2)+1}| rows, where the
+// map of J_S in degree kappa has |Homog_kappa| (a cubic fourfold: 792 against 6188).
+static bool s_smooth(const Setup &S, uint32_t Smask) {
+    const uint32_t full = (1u << S.nv) - 1, out = full & ~Smask;
+    for (uint32_t Z = out; Z; Z = (Z - 1) & out) {
+        std::vector<int> keep;
+        for (int z = 0; z < S.nv; z++)
+            if (!((Z >> z) & 1u)) keep.push_back(z);
+        const int nk = (int)keep.size();
+        const Monos me = monomials(nk, S.d - 1);
+        std::vector<std::vector<uint32_t>> forms(nk, std::vector<uint32_t>(me.count, 0));
+        std::vector<int> ex(S.nv);
+        for (int a = 0; a < nk; a++) {
+            const int i = keep[a];
+            for (int t = 0; t < S.md1.count; t++) {
+                const int *e = S.md1.at(t);
+                bool on = true;
+                for (int z = 0; z < S.nv; z++)
+                    if (((Z >> z) & 1u) && e[z]) on = false;
+                if (!on || !(S.df[i][t] % S.p)) continue;
+                for (int b = 0; b < nk; b++) ex[b] = e[keep[b]];
+                forms[a][mono_rank(ex.data(), nk, S.d - 1)] = S.df[i][t] % S.p;
+            }
+        }
+        if (!no_common_zero(nk, S.d - 1, forms, S.p)) return false;
     }
-    return (int)pivot_columns_mod_p((int)cols.size(), rows.count, A, S.p).size() == rows.count;
+    return true;
 }
 
 // Basis of Sec. 2.3: non-pivot monomials of the image of M_k, k = dm - n - 1.
@@ -296,7 +336,11 @@ static void cohomology_basis(const Setup &S, std::vector<uint32_t> &pole, std::v
         if (k < 0) continue;
         Monos rows = monomials(S.nv, k);
         std::vector<char> is_piv(rows.count, 0);
-        if (k - S.d + 1 >= 0) {
+        if (k > S.nv * (S.d - 2)) {
+            // above the socle degree (n+1)(d-2) of the Jacobian ring of a smooth f (a complete intersection
+            // of n+1 forms of degree d-1) the image of M_k is all of Homog_k: every monomial is a pivot
+            std::fill(is_piv.begin(), is_piv.end(), 1);
+        } else if (k - S.d + 1 >= 0) {
             Monos r2, src;
             std::vector<std::vector<std::pair<int, uint32_t>>> cols;
             jacobian_columns(S, k, r2, src, cols);
@@ -406,9 +450,15 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     if (Smask & ~full) { X.error = "S_mask names a variable beyond x_n"; return X.status = ZETA_ERR_ARG; }
     const uint32_t Ssize = (uint32_t)__builtin_popcount(Smask);
     if (Ssize > d) { X.error = "controlled reduction needs d >= |S| (Prop. 3.3)"; return X.status = ZETA_ERR_UNSUPPORTED; }
-    // the executor holds step matrices of side s = C(dn, n) <= 512 (cubic fourfolds: s = 3003); refused
-    // before the smoothness tests, whose eliminations grow with s
-    if (binom(d * n, n) > 512) { X.error = "step matrices larger than 512 x 512 (C(dn, n) > 512)"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    // step matrices of side s = C(dn, n): up to 512 on the persistent executors, up to 4096 on the
+    // whole-GPU one (cubic fourfolds: s = 3003), whose setup's right inverses (the section is 6188 x
+    // 18018 for a cubic fourfold) are solved on the device only; refused before the smoothness tests,
+    // whose eliminations grow with s
+    if (binom(d * n, n) > 4096) { X.error = "step matrices larger than 4096 x 4096 (C(dn, n) > 4096)"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    if (binom(d * n, n) > 512 && build_reduction && !defer_solves) {
+        X.error = "C(dn, n) > 512: the setup's right inverses are solved on the device (batch calls)";
+        return X.status = ZETA_ERR_UNSUPPORTED;
+    }
     X.n = n; X.d = d; X.p = p; X.nv = n + 1;
     X.Smask = Smask;
     X.base = Ssize - 1;
@@ -420,14 +470,7 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     setup_poly(S, hs);
     if (!smooth(S)) { X.error = "f is not smooth (Jacobian criterion)"; return X.status = ZETA_ERR_NOT_SMOOTH; }
     X.kappa = (n + 1) * (d - 1) + 1 - Ssize;
-    // deferred: the section's rank decides (the unit-pivot elimination over Z/q reaches full rank iff
-    // the map is onto mod p), unless an earlier error is returned first
-    X.s_smooth_deferred = defer_solves && build_reduction && Smask != full;
-    auto not_s_smooth = [&]() {
-        if (!s_smooth(S, Smask, (int)X.kappa)) { X.error = "f is not S-smooth (Definition 3.1)"; return true; }
-        return false;
-    };
-    if (Smask != full && !X.s_smooth_deferred && !s_smooth(S, Smask, (int)X.kappa)) {
+    if (Smask != full && !s_smooth(S, Smask)) {
         X.error = "f is not S-smooth (Definition 3.1)";
         return X.status = ZETA_ERR_NOT_SMOOTH;
     }
@@ -459,18 +502,10 @@ zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *op
     X.M = (uint32_t)Mp;
     // the device keeps residues mod q as two 30-bit limbs (vector path) or at most
     // eight balanced base-256 digits (tensor-core path): q < 2^60
-    if (!pow_fits(p, X.M, (uint64_t)1 << 60, &X.q)) {
-        if (X.s_smooth_deferred && not_s_smooth()) return X.status = ZETA_ERR_NOT_SMOOTH;
-        X.error = "p^M exceeds 2^60";
-        return X.status = ZETA_ERR_PRECISION;
-    }
+    if (!pow_fits(p, X.M, (uint64_t)1 << 60, &X.q)) { X.error = "p^M exceeds 2^60"; return X.status = ZETA_ERR_PRECISION; }
     for (uint32_t m = 1; m <= n; m++) {
         uint64_t tmp;
-        if (X.N[m - 1] && !pow_fits(p, X.N[m - 1] + m - 1, (uint64_t)1 << 63, &tmp)) {
-            if (X.s_smooth_deferred && not_s_smooth()) return X.status = ZETA_ERR_NOT_SMOOTH;
-            X.error = "p^s exceeds 2^63";
-            return X.status = ZETA_ERR_PRECISION;
-        }
+        if (X.N[m - 1] && !pow_fits(p, X.N[m - 1] + m - 1, (uint64_t)1 << 63, &tmp)) { X.error = "p^s exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
     }
     if (!build_reduction) { X.ms_setup = now_ms() - t0; return ZETA_OK; }
 
@@ -561,11 +596,7 @@ static zeta_status complete_reduction(const Setup &S, Instance &X, double t0) {
         }
     {
         SolveJob &J = X.solves[0];
-        if (!J.ok) {
-            if (X.s_smooth_deferred) { X.error = "f is not S-smooth (Definition 3.1)"; return X.status = ZETA_ERR_NOT_SMOOTH; }
-            X.error = "section: Jacobian map not onto";
-            return X.status = ZETA_ERR_INTERNAL;
-        }
+        if (!J.ok) { X.error = "section: Jacobian map not onto"; return X.status = ZETA_ERR_INTERNAL; }
         const int R = J.R, C = J.C;
         const Monos src = monomials(nv, (int)X.kappa - (int)d + 1);
         X.sec_rows = C;
@@ -625,11 +656,13 @@ static zeta_status complete_reduction(const Setup &S, Instance &X, double t0) {
                 Level &L = lev[m];
                 if (L.rows.count == 0) break;
                 int R = L.rows.count, C = L.ncols;
+                std::vector<int> nzr;
+                for (int r2 = 0; r2 < R; r2++)
+                    if (vec[r2]) nzr.push_back(r2);
                 std::vector<uint64_t> sol(C, 0);
                 for (int c = 0; c < C; c++) {
                     uint64_t acc = 0;
-                    for (int r2 = 0; r2 < R; r2++)
-                        if (vec[r2]) acc = mq.add(acc, mq.mul(L.Xinv[(size_t)c * R + r2], vec[r2]));
+                    for (int r2 : nzr) acc = mq.add(acc, mq.mul(L.Xinv[(size_t)c * R + r2], vec[r2]));
                     sol[c] = acc;
                 }
                 for (int c = 0; c < L.nb; c++) X.fin[(size_t)L.bcols[c] * X.h_rows + h] = mq.from(sol[c]);
@@ -865,7 +898,25 @@ zeta_status finish_instance(Instance &X) {
     int K = 0;
     for (uint32_t i = 0; i <= b / 2; i++) K = std::max(K, e[i]);
     uint64_t pK;
-    if (!pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK)) { X.error = "charpoly precision exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
+    if (!pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK)) {
+        // a run below the precision rule (relative precision rmin) knows a_i only mod p^(rmin + H(i)), H the
+        // Hodge polygon (the slopes n - m of the basis elements in increasing order): the charpoly is then
+        // taken mod the largest power of p below 2^63 when that power covers those digits
+        std::vector<int> slope;
+        for (uint32_t col = 0; col < b; col++) slope.push_back((int)n - (int)X.pole[col]);
+        std::sort(slope.begin(), slope.end());
+        int need = 0, H = 0;
+        for (uint32_t i = 1; i <= b / 2; i++) {
+            H += slope[i - 1];
+            need = std::max(need, std::min(e[i], (int)rmin + H));
+        }
+        int Kfit = 0;
+        while (pow_fits(p, (uint32_t)Kfit + 1, (uint64_t)1 << 63, &pK)) Kfit++;
+        if (need > Kfit) { X.error = "charpoly precision exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
+        K = Kfit;
+        for (auto &x : e) x = std::min(x, K);
+        pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK);
+    }
     std::vector<uint64_t> cp = berkowitz_mod(X.F, (int)b, pK);
     // eps = (-1)^b det(C) mod p^{min r_m}
     uint64_t pr;

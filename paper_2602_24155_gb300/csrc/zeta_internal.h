@@ -109,7 +109,6 @@ struct Instance {
     // right inverses of the reduction build: [0] the section, [m] the final reduction at pole order m
     std::vector<SolveJob> solves;
     bool solves_pending = false;      // prepare_instance stopped before using them (prepare_complete resumes)
-    bool s_smooth_deferred = false;   // the S-smoothness test is the section's rank (ZETA_ERR_NOT_SMOOTH if short)
     Plan plan;
     PolicyNet net;              // learned policy (ZETA_POLICY_LEARNED)
     // per level t: exponent -> terms reaching it in the reference game (the cover game with Algorithm 3), and
@@ -137,7 +136,7 @@ struct Instance {
 // Host-side steps (zeta_host.cpp)
 // defer_solves: stop once the right inverses' matrices are built (X.solves, X.solves_pending), so that
 // they can be solved together on the device; prepare_complete solves what is left on the host and
-// finishes the reduction data.  The S-smoothness test is then read from the section's rank.
+// finishes the reduction data.
 zeta_status prepare_instance(const zeta_hypersurface *hs, const zeta_options *opt,
                              bool build_reduction, Instance &X, bool defer_solves = false);
 zeta_status prepare_complete(Instance &X);
@@ -190,6 +189,8 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
                           const uint64_t *q, std::string &err);
 // Solves the jobs on the device (zeta_setup.cuh), each modulo qs[t] with unit test mod ps[t];
 // sets done, ok (full row rank) and X.  Jobs too wide for the kernel's shared memory are left undone.
+// Runs one instance's plan on the whole-GPU executor (zeta_large.cuh), fills X.H; s <= 4096, q < 2^56.
+zeta_status engine_run_large(DeviceEngine *e, Instance &X, std::string &err, double *ms_device, uint64_t *launches);
 zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, const std::vector<uint64_t> &qs,
                          const std::vector<uint64_t> &ps, std::string &err, double *ms_device);
 

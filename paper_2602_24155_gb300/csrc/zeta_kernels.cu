@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(TC ? kTcThreads : 512) __maxnreg__(TC ? 255 : 
 }  // namespace zeta
 #include "zeta_cluster.cuh"
 #include "zeta_setup.cuh"
+#include "zeta_large.cuh"
 namespace zeta {
 
 // Kernel-level Algorithm 2 on independent problems (zeta_horner_device):
@@ -1451,6 +1452,180 @@ zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, c
         J.done = true;
     }
     return ZETA_OK;
+}
+
+// Whole-GPU executor (zeta_large.cuh): the host walks the plan and launches, on the engine's stream, per entry
+// the formation of W (arrival block, start terms), per chunk the generation of A and M(k-1) and one step kernel
+// per step (per group of eight columns), and the merge or the numerators.  Fills X.H; ms_device = the plan's
+// time between CUDA events on the stream.
+template <typename T, bool NARROW>
+static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err, double *ms_device, uint64_t *launches) {
+    if (ms_device) *ms_device = 0;
+    if (launches) *launches = 0;
+    uint64_t nl = 0;
+    CUDA_TRY(cudaSetDevice(e->device));
+    const int s = (int)X.s, b = (int)X.b, nv = (int)X.nv;
+    if (s < 1 || s > 4096 || b < 1 || b > 32 || X.q >= ((uint64_t)1 << 56) || X.sec.empty()) {
+        err = "whole-GPU executor: needs s <= 4096, b <= 32, q < 2^56";
+        return ZETA_ERR_UNSUPPORTED;
+    }
+    zeta_status st = upload_binom(e, err);
+    if (st) return st;
+    const ModQ Q = make_modq(X.q);
+    // Sec R mod q (Sec R^2 mod q for the narrow path, whose generation ends with one REDC)
+    std::vector<T> secR(X.sec.size());
+    {
+        const u128 Rm = ((u128)1 << 64) % X.q;
+        const u128 Rk = NARROW ? Rm * Rm % X.q : Rm;
+        for (size_t t = 0; t < X.sec.size(); t++) secR[t] = (T)((u128)X.sec[t] * Rk % X.q);
+    }
+    T *d_sec, *d_M, *d_A;
+    uint64_t *d_W, *d_V, *d_H, *d_blocks;
+    int32_t *d_monoS, *d_secrow, *d_colidx;
+    Term *d_terms;
+    if ((st = upload(e, "lg_sec", secR, &d_sec, err))) return st;
+    std::vector<T>().swap(secR);
+    if ((st = upload(e, "lg_monoS", X.tab_monoS, &d_monoS, err))) return st;
+    if ((st = upload(e, "lg_secrow", X.tab_secrow, &d_secrow, err))) return st;
+    if ((st = upload(e, "lg_terms", X.terms, &d_terms, err))) return st;
+    const int sp = NARROW ? (s + 3) & ~3 : s;  // row stride of M and A, column stride of W and V
+    const size_t ss = (size_t)s * sp, block_words = (size_t)s * b;
+    const size_t cap = std::max<size_t>(X.plan.cap, 1);
+    if ((st = ensure(e, "lg_M", sizeof(T) * ss, (void **)&d_M, err))) return st;
+    if ((st = ensure(e, "lg_A", sizeof(T) * ss, (void **)&d_A, err))) return st;
+    if ((st = ensure(e, "lg_colidx", sizeof(int32_t) * s, (void **)&d_colidx, err))) return st;
+    if ((st = ensure(e, "lg_W", sizeof(uint64_t) * sp * b, (void **)&d_W, err))) return st;
+    if ((st = ensure(e, "lg_V", sizeof(uint64_t) * sp * b, (void **)&d_V, err))) return st;
+    if ((st = ensure(e, "lg_H", sizeof(uint64_t) * X.h_rows * b, (void **)&d_H, err))) return st;
+    if ((st = ensure(e, "lg_blocks", sizeof(uint64_t) * 2 * cap * block_words, (void **)&d_blocks, err))) return st;
+    cudaStream_t stream = e->stream;
+    CUDA_TRY(cudaMemsetAsync(d_H, 0, sizeof(uint64_t) * X.h_rows * b, stream));
+    CUDA_TRY(cudaMemsetAsync(d_W, 0, sizeof(uint64_t) * sp * b, stream));  // the padding rows stay zero
+    CUDA_TRY(cudaMemsetAsync(d_V, 0, sizeof(uint64_t) * sp * b, stream));
+    std::vector<uint64_t> tR(64, 0);  // t R mod q, the step index within a chunk in Montgomery form
+    for (int t = 0; t < 64; t++) tR[t] = (uint64_t)(((u128)t << 64) % X.q);
+    cudaEvent_t ev[2];
+    CUDA_TRY(cudaEventCreate(&ev[0]));
+    CUDA_TRY(cudaEventCreate(&ev[1]));
+    CUDA_TRY(cudaEventRecord(ev[0], stream));
+    auto blocks_for = [](size_t n, int t) { return (unsigned)((n + t - 1) / t); };
+    const unsigned step_grid = blocks_for((size_t)s, kLgWarps);
+    const int hdeg = (int)(X.d * X.n - X.n - 1);
+    const Plan &P = X.plan;
+    cudaError_t le = cudaSuccess;
+    for (size_t ph = 0; ph + 1 < P.phase_begin.size() && le == cudaSuccess; ph++) {
+        uint64_t *cur = d_blocks + (ph & 1 ? cap * block_words : 0);
+        uint64_t *nxt = d_blocks + (ph & 1 ? 0 : cap * block_words);
+        for (uint32_t ei = P.phase_begin[ph]; ei < P.phase_begin[ph + 1] && le == cudaSuccess; ei++) {
+            const PlanEntry &E = P.entries[ei];
+            LgCols cm;
+            for (int t = 0; t < 32; t++) cm.col[t] = cm.lc[t] = -1;
+            cm.c = 0;
+            for (int col = 0; col < b; col++)
+                if (E.live >> col & 1u) {
+                    cm.lc[col] = cm.c;
+                    cm.col[cm.c++] = col;
+                }
+            if ((E.arrival >= 0 && (size_t)E.arrival >= cap) || (E.dest >= 0 && (size_t)E.dest >= cap) ||
+                (E.start_chain >= 0 && (size_t)E.start_chain >= X.chains.size())) {
+                err = "whole-GPU executor: plan entry out of range";
+                le = cudaErrorInvalidValue;
+                break;
+            }
+            if (cm.c == 0) {  // nothing carried: only a first contribution's clearing of its block remains
+                if (E.dest >= 0 && (E.flags & 1u))
+                    le = cudaMemsetAsync(nxt + (size_t)E.dest * block_words, 0, sizeof(uint64_t) * block_words, stream);
+                continue;
+            }
+            nl++;
+            k_lg_form<<<blocks_for((size_t)cm.c * s, 256), 256, 0, stream>>>(
+                s, sp, b, cm, E.arrival >= 0 ? cur + (size_t)E.arrival * block_words : nullptr, d_W);
+            if (E.start_chain >= 0) {
+                const Chain &C = X.chains[E.start_chain];
+                if (C.term_end > C.term_begin && ++nl)
+                    k_lg_terms<<<blocks_for(C.term_end - C.term_begin, 256), 256, 0, stream>>>(
+                        sp, cm, d_terms, C.term_begin, C.term_end, d_W, X.q);
+            }
+            LgVec U;
+            for (int t = 0; t < kMaxVars; t++) U.x[t] = t < nv ? E.U[t] : 0;
+            uint64_t *W = d_W, *V = d_V;
+            for (uint32_t ci = E.chunk_begin; ci < E.chunk_end; ci++) {
+                const PlanChunk &CH = P.chunks[ci];
+                LgVec v;
+                for (int t = 0; t < kMaxVars; t++) v.x[t] = t < nv ? CH.v[t] : 0;
+                nl += 2;
+                k_lg_colidx<<<blocks_for((size_t)s, 256), 256, 0, stream>>>(s, nv, (int)X.kappa, d_monoS, v, d_colidx);
+                if constexpr (NARROW)
+                    k_lg_gen_narrow<<<blocks_for(ss, 256), 256, 0, stream>>>(
+                        s, sp, nv, X.sec_cols, d_monoS, d_secrow, d_colidx, (const uint32_t *)d_sec, U, v, Q,
+                        (uint32_t *)d_M, (uint32_t *)d_A);
+                else
+                    k_lg_gen<T><<<blocks_for(ss, 256), 256, 0, stream>>>(s, nv, X.sec_cols, d_monoS, d_secrow, d_colidx,
+                                                                         d_sec, U, v, Q, d_M, d_A);
+                if (NARROW && CH.k > 64) {
+                    err = "whole-GPU executor: chunk longer than 64 steps";
+                    le = cudaErrorInvalidValue;
+                    break;
+                }
+                for (int y = 0; y < CH.k; y++) {
+                    for (int c0 = 0; c0 < cm.c; c0 += kLgMaxCpt) {
+                        const int cg = std::min(kLgMaxCpt, cm.c - c0);
+                        const uint64_t *Wg = W + (size_t)c0 * sp;
+                        uint64_t *Vg = V + (size_t)c0 * sp;
+                        nl++;
+                        if constexpr (NARROW) {
+                            const uint32_t *Mn = (const uint32_t *)d_M, *An = (const uint32_t *)d_A;
+                            const uint64_t t = tR[y];
+                            if (cg == 1) k_lg_step_narrow<1><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
+                            else if (cg == 2) k_lg_step_narrow<2><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
+                            else if (cg <= 4) k_lg_step_narrow<4><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
+                            else k_lg_step_narrow<8><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
+                        } else {
+                            const int last = c0 + kLgMaxCpt >= cm.c;
+                            if (cg == 1) k_lg_step<1, T><<<step_grid, kLgWarps * 32, 0, stream>>>(s, cg, Wg, Vg, d_M, d_A, Q, last);
+                            else if (cg == 2) k_lg_step<2, T><<<step_grid, kLgWarps * 32, 0, stream>>>(s, cg, Wg, Vg, d_M, d_A, Q, last);
+                            else if (cg <= 4) k_lg_step<4, T><<<step_grid, kLgWarps * 32, 0, stream>>>(s, cg, Wg, Vg, d_M, d_A, Q, last);
+                            else k_lg_step<8, T><<<step_grid, kLgWarps * 32, 0, stream>>>(s, cg, Wg, Vg, d_M, d_A, Q, last);
+                        }
+                    }
+                    std::swap(W, V);
+                }
+                for (int t = 0; t < nv; t++) U.x[t] -= CH.k * CH.v[t];
+            }
+            if (le != cudaSuccess) break;
+            nl++;
+            if (E.dest < 0)
+                k_lg_numer<<<blocks_for((size_t)cm.c * s, 256), 256, 0, stream>>>(s, sp, b, nv, hdeg, U, d_monoS, cm, W, d_H,
+                                                                                 X.q);
+            else
+                k_lg_merge<<<blocks_for(block_words, 256), 256, 0, stream>>>(s, sp, b, cm, W, nxt + (size_t)E.dest * block_words,
+                                                                            (int)(E.flags & 1u), X.q);
+            le = cudaGetLastError();
+        }
+    }
+    if (le == cudaSuccess) le = cudaEventRecord(ev[1], stream);
+    X.H.assign((size_t)X.h_rows * b, 0);
+    if (le == cudaSuccess)
+        le = cudaMemcpyAsync(X.H.data(), d_H, sizeof(uint64_t) * X.H.size(), cudaMemcpyDeviceToHost, stream);
+    if (le == cudaSuccess) le = cudaStreamSynchronize(stream);
+    float ms = 0;
+    if (le == cudaSuccess) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (le == cudaErrorInvalidValue && !err.empty()) return ZETA_ERR_INTERNAL;
+    CUDA_TRY(le);
+    if (ms_device) *ms_device = ms;
+    if (launches) *launches = nl;
+    X.steps = P.steps;
+    X.column_steps = P.column_steps;
+    X.chunks = P.chunks_played;
+    return ZETA_OK;
+}
+
+zeta_status engine_run_large(DeviceEngine *e, Instance &X, std::string &err, double *ms_device, uint64_t *launches) {
+    if (X.q < ((uint64_t)1 << 26)) return run_large_impl<uint32_t, true>(e, X, err, ms_device, launches);
+    return X.q < ((uint64_t)1 << 32) ? run_large_impl<uint32_t, false>(e, X, err, ms_device, launches)
+                                     : run_large_impl<uint64_t, false>(e, X, err, ms_device, launches);
 }
 
 // ---------------------------------------------------------------------------

@@ -159,6 +159,31 @@ def k3_height(P, p, r=1):
     return None
 
 
+def hodge_polygon(n, d):
+    """H(i), i = 0..b: the Hodge polygon's height, the sum of the i smallest Hodge slopes (n - m for the basis
+    elements of pole order m)."""
+    slopes = []
+    for m, k in sorted(hodge_numbers(n, d).items(), reverse=True):
+        slopes += [n - m] * k
+    H = [0]
+    for sl in slopes:
+        H.append(H[-1] + sl)
+    return H
+
+
+def fourfold_height(P, p, r=1):
+    """Height of a cubic fourfold (Hodge numbers 1, 20, 1 on primitive H^4: a K3 surface's shape with every slope
+    raised by one) from P(T) at relative precision r.  The Hodge polygon has H(i) = 2i - 1 for 1 <= i <= 21, so a_i
+    is known mod p^(r + 2i - 1).  A fourfold of finite height h has Newton slopes 2 - 1/h (h times), 2, ..., 2 + 1/h
+    (h times): its polygon passes through (h, 2h - 1) and lies strictly above y = 2i - 1 before it, so h is the
+    least i with v_p(a_i) <= 2i - 1, which a_i mod p^(2i) decides.  Returns h in 1..11, or None (supersingular)."""
+    for i in range(1, 12):
+        a = int(P[i]) % p ** (r + 2 * i - 1)
+        if a and vp(a, p) <= 2 * i - 1:
+            return i
+    return None
+
+
 def k3_heights(ctx, specs, policy="p_chunk", path="vector"):
     """Heights of quartic K3 surfaces from one precision-1 batch.  Returns (heights, per-instance stats, total stats):
     heights[i] is 1..10, 'inf' for a supersingular surface, or None if the instance failed (e.g. not smooth)."""

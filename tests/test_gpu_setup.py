@@ -3,8 +3,7 @@
 Both run Gauss-Jordan over Z/q with unit pivots in column order, the first unit row as pivot (the section of
 Prop. 3.3 and the final reduction's levels, Sec. 3.3 step (2)); with exact arithmetic the section and the final
 reduction map must agree word for word.  Batches whose setup is solved either way must return the same P(T)
-and the same statuses, including ZETA_ERR_NOT_SMOOTH for a smooth cubic surface that is not {3}-smooth (the
-device path reads S-smoothness from the section's rank instead of the host's separate test).
+and the same statuses, including ZETA_ERR_NOT_SMOOTH for two smooth cubic surfaces that are not {3}-smooth.
 """
 import os
 import time

@@ -1,0 +1,84 @@
+"""The whole-GPU executor (zeta_large.cuh) against the persistent executors, and the cubic fourfold it is built for.
+
+ - Quintic curves, cubic surfaces (S = {3}), a K3 surface and a cubic threefold (S = {4}) at relative precision 1:
+   the same batch run with ZETA_FLAG_WHOLE_GPU and without gives the same P(T) word for word (the same plan in exact
+   arithmetic, so the same numerators H).
+ - The Fermat cubic fourfold over F_7 (s = C(15, 5) = 3003, b = 22, S = {5}) at relative precision 1 (M = 9): its
+   P(T) agrees with Weil's Gauss-sum closed form (computed without any of the reduction) modulo p^(1 + H(i)) in
+   every coefficient, H the Hodge polygon (0, 1, 3, ..., 41, 44); its height is 1 (p = 1 mod 3: ordinary).
+"""
+import os
+
+import pytest
+
+import zeta_inputs as zi
+from oracle import pins
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+z = pytest.importorskip("paper_2602_24155_gb300")
+
+GOLDEN_3FOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cubic_threefold_f11.txt")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = z.zeta_create(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    z.zeta_destroy(c)
+
+
+def _accept(n, d, p, c):
+    try:
+        z.zeta_query((n, d, p, c))
+        return True
+    except z.ZetaError:
+        return False
+
+
+def _threefold():
+    out = {}
+    for line in open(GOLDEN_3FOLD):
+        if line.startswith("#") or ":" not in line:
+            continue
+        key, _, val = line.partition(":")
+        out[key.strip()] = val.strip()
+    n, d, p = map(int, out["n d p"].split())
+    return n, d, p, [int(x) for x in out["coeffs"].split()]
+
+
+def test_whole_gpu_executor_equals_the_persistent_ones(ctx):
+    specs = [zi.draw_instance("quintic_curves", i, _accept)[:4] for i in (0, 5, 11)]
+    specs += [zi.draw_instance("cubic_surfaces", i, _accept)[:4] for i in (0, 1)]
+    specs.append(zi.draw_instance("quartic_k3", 9, _accept)[:4])
+    specs.append(_threefold())
+    P0, per0, tot0 = z.zeta_batch(ctx, specs, policy="p_chunk", r=1)
+    P1, per1, tot1 = z.zeta_batch(ctx, specs, policy="p_chunk", r=1, whole_gpu=True)
+    assert [x["status"] for x in per0] == [0] * len(specs)
+    assert [x["status"] for x in per1] == [0] * len(specs)
+    assert P0 == P1
+    assert tot1["column_steps"] == tot0["column_steps"]
+    print("whole-GPU executor: %d launches, %.1f ms; persistent: %.1f ms"
+          % (tot1["kernel_launches"], tot1["ms_kernel"], tot0["ms_kernel"]))
+
+
+def test_fermat_cubic_fourfold_f7_relative_precision_one(ctx):
+    from paper_2602_24155_gb300.newton import fourfold_height, hodge_polygon
+    n, d, p = 5, 3, 7
+    P, per, tot = z.zeta_batch(ctx, [(n, d, p, zi.fermat(n, d))], policy="p_chunk", r=1)
+    st = per[0]
+    print("Fermat cubic fourfold over F_7, r = 1: status %d, s %d, b %d, M %d; %d chunks, %d steps, %d column steps; "
+          "setup %.0f ms, kernels %.0f ms in %d launches" % (st["status"], st["s"], st["b"], st["M"], tot["chunks"],
+                                                            tot["steps"], tot["column_steps"], tot["ms_host_setup"],
+                                                            tot["ms_kernel"], tot["kernel_launches"]))
+    assert st["status"] == 0 and st["s"] == 3003 and st["b"] == 22 and st["M"] == 9
+    exact = pins.fermat_charpoly(n, d, p)
+    H = hodge_polygon(n, d)
+    assert len(P[0]) == len(exact) == 23 and P[0][0] == 1
+    for i in range(1, 23):
+        mod = p ** (1 + H[i])
+        assert (P[0][i] - exact[i]) % mod == 0, i
+    assert fourfold_height(P[0], p) == 1

@@ -413,8 +413,13 @@ def test_general_S_refusals():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_query(spec, S=(0, 1, 2, 3))            # |S| = 4 > d = 3
     assert e.value.status == 3
+    fermat4 = (5, 3, 7, zi.fermat(5, 3))               # cubic fourfold: s = C(15, 5) = 3003
     with pytest.raises(z.ZetaError) as e:
-        z.zeta_query((5, 3, 7, zi.fermat(5, 3)))      # cubic fourfold: s = C(15, 5) = 3003 > 512
+        z.zeta_query(fermat4)                          # full precision: p^M = 7^25 > 2^60
+    assert e.value.status == 4
+    assert z.zeta_query(fermat4, r=1) == (22, 1, 9, 3003)   # b, r, M, s at relative precision 1
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_plan(fermat4, r=1)                      # s > 512: the right inverses are solved on the device only
     assert e.value.status == 3
 
 
