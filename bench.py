@@ -320,6 +320,92 @@ def _mixed_stream(z, ctx, stream, torch):
             "busy_ms_median_by_class": {k: statistics.median(v) for k, v in sorted(by_class.items())}}
 
 
+def _accept_r1(z):
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c), r=1)
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    return accept
+
+
+def _quintic_surfaces(z, ctx, stream, torch, count, train_count):
+    """Dense quintic surfaces over F_7 (n = 3, d = 5: b = 52 columns, s = 455) at relative precision 1 (M = 3: P(T)
+    mod p, the unit-root part; the full precision needs p^M = 7^49, beyond 64-bit residues), on the whole-GPU
+    executor, with the learned policy (a network trained here on rollouts of the surfaces' own cover games, indices
+    past the batch) against the method without it (cover) and p-chunk.  P(T) mod p of these surfaces equals the
+    Hasse-Witt closed form in tests/test_gpu_quintic_surfaces.py."""
+    from paper_2602_24155_gb300.newton import unit_roots_mod_p
+    from paper_2602_24155_gb300.policy_train import train_policy
+    accept = _accept_r1(z)
+    specs = [zi.draw_instance("quintic_surfaces", i, accept)[:4] for i in range(count)]
+    train = [zi.draw_instance("quintic_surfaces", 100000 + i, accept)[:4] for i in range(train_count)]
+    t0 = time.perf_counter()
+    weights, loss, decisions = train_policy(ctx, train, hidden=8, epochs=60, opt=dict(r=1))
+    out = {"workload": "quintic_surfaces_%d" % count, "precision": "relative precision r = 1 (M = 3)",
+           "training": {"instances": train_count, "decisions": decisions, "loss": loss,
+                        "s": time.perf_counter() - t0}}
+    P_ref = None
+    for pol in ("learned", "cover", "p_chunk"):
+        o = dict(policy=pol, r=1)
+        if pol == "learned":
+            o.update(weights=weights, hidden=8)
+        plan = z.zeta_batch_prepare(ctx, specs, **o)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        P, per, tot = plan.finish()
+        plan.release()
+        ms = e0.elapsed_time(e1)
+        if P_ref is None:
+            P_ref = P
+        assert P == P_ref, "policies disagree"
+        out[pol] = {"zeta_per_s": len(specs) / (ms / 1000.0), "ms": ms, "column_steps": tot["column_steps"],
+                    "chunks": tot["chunks"], "steps": tot["steps"], "kernel_launches": tot["kernel_launches"],
+                    "ms_host_setup": tot["ms_host_setup"]}
+    out["network_gain_over_cover"] = {
+        "column_steps": 1 - out["learned"]["column_steps"] / out["cover"]["column_steps"],
+        "time": 1 - out["learned"]["ms"] / out["cover"]["ms"]}
+    hist = {}
+    for P in P_ref:
+        k = unit_roots_mod_p(P, 7)
+        hist[k] = hist.get(k, 0) + 1
+    out["unit_roots_histogram"] = dict(sorted(hist.items()))
+    return out
+
+
+def _cubic_fourfolds(z, ctx, stream, torch, dense):
+    """Cubic fourfolds over F_7 (n = 5, d = 3: s = C(15, 5) = 3003, b = 22, S = {5}) at relative precision 1 (M = 9;
+    the full precision needs 7^25, beyond 64-bit residues) on the whole-GPU executor: the Fermat cubic fourfold and,
+    with `dense`, the dense one of tests/golden/cubic_fourfold_f7.txt (dense_candidate seed 5, instance 76).  The
+    height (first slope 2 - 1/h) is what relative precision 1 decides.  Checks: tests/test_gpu_whole.py (Gauss-sum
+    closed form) and tests/test_gpu_fourfold.py (point counts over F_7 and F_49)."""
+    from paper_2602_24155_gb300.newton import fourfold_height
+    cases = [("fermat", zi.fermat(5, 3))]
+    if dense:
+        cases.append(("dense_seed5_76", zi.dense_candidate(5, 3, 7, 5, 76, 0)))
+    out = {}
+    for name, c in cases:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P, per, tot = z.zeta_batch(ctx, [(5, 3, 7, c)], policy="p_chunk", r=1)
+        wall = time.perf_counter() - t0
+        out[name] = {"status": per[0]["status"], "wall_s": wall, "ms_host_setup": tot["ms_host_setup"],
+                     "ms_kernel": tot["ms_kernel"], "kernel_launches": tot["kernel_launches"],
+                     "chunks": tot["chunks"], "steps": tot["steps"], "column_steps": tot["column_steps"],
+                     "column_steps_per_s": tot["column_steps"] / (tot["ms_kernel"] / 1000.0),
+                     "modmac_per_s": tot["column_steps"] * 3003.0 * 3003.0 / (tot["ms_kernel"] / 1000.0),
+                     "height": fourfold_height(P[0], 7) if P[0] else None}
+    return out
+
+
 def _cubic_survey(z, ctx, stream, torch):
     """1024 dense cubic surfaces over F_7, F_11, F_13 at full precision in one persistent launch: d = 3 < n + 1, so
     the reduction runs with S = {3} (Prop. 3.3 for a smaller index set; same kernel, section of J_S).  Parity with
@@ -394,6 +480,11 @@ def main():
     ap.add_argument("--k3-N", type=int, default=0,
                     help="truncate the K3 line's series orders to N (small profiling case; 0 = full precision)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed stream")
+    ap.add_argument("--no-fourfold", action="store_true", help="skip the cubic fourfold line (Fermat, r = 1)")
+    ap.add_argument("--fourfold-dense", action="store_true",
+                    help="add the dense cubic fourfold to the fourfold line (several minutes)")
+    ap.add_argument("--surface-count", type=int, default=256,
+                    help="quintic surfaces over F_7 at r = 1 with learned / cover / p-chunk (0 = skip)")
     ap.add_argument("--no-cubic", action="store_true",
                     help="skip the cubic-surface line (1024 surfaces, S = {3}, full precision)")
     args = ap.parse_args()
@@ -601,6 +692,16 @@ def main():
             line["cubic_surfaces"] = _cubic_survey(z, ctx, stream, torch)
         except Exception as exc:   # reported, never a reason to lose the main line
             line["cubic_surfaces"] = {"error": repr(exc)[:200]}
+    if rank == 0 and world == 1 and args.surface_count > 0:
+        try:
+            line["quintic_surfaces"] = _quintic_surfaces(z, ctx, stream, torch, args.surface_count, 24)
+        except Exception as exc:   # reported, never a reason to lose the main line
+            line["quintic_surfaces"] = {"error": repr(exc)[:200]}
+    if rank == 0 and world == 1 and not args.no_fourfold:
+        try:
+            line["cubic_fourfolds"] = _cubic_fourfolds(z, ctx, stream, torch, args.fourfold_dense)
+        except Exception as exc:   # reported, never a reason to lose the main line
+            line["cubic_fourfolds"] = {"error": repr(exc)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sample_n = max(1, min(cores, 16))

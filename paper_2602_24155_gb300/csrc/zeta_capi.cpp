@@ -186,7 +186,7 @@ zeta_status zeta_charpoly(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta
 struct zeta_batch_plan {
     std::vector<Instance> inst;
     std::vector<Instance *> ok;
-    std::vector<Instance *> large;  // run one at a time on the whole-GPU executor (s > 512, or ZETA_FLAG_WHOLE_GPU)
+    std::vector<Instance *> large;  // one at a time on the whole-GPU executor (s > 512, b > 32, ZETA_FLAG_WHOLE_GPU)
     zeta_options opt;
     DeviceBatch *dev = nullptr;
     double ms_setup = 0, ms_device = 0, ms_large = 0;
@@ -301,7 +301,7 @@ static zeta_status batch_prepare_lane(zeta_ctx *ctx, const zeta_hypersurface *hs
     P->ms_setup = now_ms() - t0;
     std::vector<Instance *> small;
     for (Instance *X : P->ok)
-        if (X->s > 512 || (P->opt.flags & ZETA_FLAG_WHOLE_GPU)) P->large.push_back(X);
+        if (X->s > 512 || X->b > 32 || (P->opt.flags & ZETA_FLAG_WHOLE_GPU)) P->large.push_back(X);
         else small.push_back(X);
     if (!small.empty()) {
         resolve_path(ctx, small, P->opt);
@@ -620,6 +620,7 @@ zeta_status zeta_plan_moves(const zeta_hypersurface *hs, const zeta_options *opt
     zeta_status st = prepare_instance(hs, &o, true, X);
     if (!st) st = schedule_policy(X, o.policy);
     if (st) return st;
+    if (X.b > 32) return ZETA_ERR_UNSUPPORTED;  // `live` is exported as one 32-bit word
     const Plan &P = X.plan;
     const size_t nv = X.nv;
     *nphases = P.phase_begin.size() - 1;

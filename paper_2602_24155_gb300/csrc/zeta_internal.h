@@ -51,7 +51,7 @@ struct PlanEntry {
     int32_t start_chain;         // chain whose start terms join here, or -1
     int32_t dest;                // block of the next phase buffer, -1: pole order n reached
     uint32_t flags;              // bit 0: first contribution to dest (store, not add)
-    uint32_t live;               // basis columns carried (bit mask, b <= 32)
+    uint64_t live;               // basis columns carried (bit mask, b <= 64)
 };
 
 struct Plan {
@@ -114,9 +114,9 @@ struct Instance {
     // per level t: exponent -> terms reaching it in the reference game (the cover game with Algorithm 3), and
     // for each basis column the number of those terms that carry it
     std::vector<std::unordered_map<uint64_t, int>> ref_contrib;
-    std::vector<std::unordered_map<uint64_t, std::array<uint16_t, 32>>> ref_cols;
+    std::vector<std::unordered_map<uint64_t, std::array<uint16_t, 64>>> ref_cols;
     // columns carried by the term whose chunk direction is being chosen (set by the scheduler before it asks)
-    mutable uint32_t cur_live = 0;
+    mutable uint64_t cur_live = 0;
     // ZETA_POLICY_COVER with a decision hook: the hook chooses the direction of every chunk decision
     // (U, steps left in the p-chunk, level t); false = Algorithm 3 (training-data rollouts)
     std::function<bool(const int32_t *U, int left, int t, int *v)> hook;

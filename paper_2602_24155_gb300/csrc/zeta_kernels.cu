@@ -965,7 +965,7 @@ zeta_status engine_prepare(DeviceEngine *e, std::vector<Instance *> &batch, zeta
             de.start_chain = pe.start_chain;
             de.dest = pe.dest;
             de.flags = pe.flags;
-            de.live = pe.live;
+            de.live = (uint32_t)pe.live;  // b <= 32 on the persistent executors
             dentries.push_back(de);
         }
         for (const PlanChunk &pc : X->plan.chunks) {
@@ -1400,36 +1400,75 @@ zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, c
     }
     if (descs.empty()) return ZETA_OK;
     const uint32_t count = (uint32_t)descs.size();
+    // a few matrices with R >= 1000 rows (a cubic threefold's section, a cubic fourfold's section and its final
+    // level m = 5) take the whole GPU, one at a time; the others, or many large ones, one block each in a single
+    // launch
+    uint32_t nlarge = 0;
+    for (const SolveDesc &d : descs) nlarge += d.R >= 1000;
+    std::vector<SolveDesc> small_descs;
+    std::vector<uint32_t> small_of, big_of;
+    for (uint32_t t = 0; t < count; t++) {
+        if (descs[t].R >= 1000 && nlarge <= 8) big_of.push_back(t);
+        else {
+            small_of.push_back(t);
+            small_descs.push_back(descs[t]);
+        }
+    }
     SolveDesc *d_desc;
     uint32_t *d_idx;
     uint64_t *d_val, *d_work, *d_out;
     int32_t *d_piv, *d_rank;
+    SolveState *d_state;
     zeta_status st;
-    if ((st = upload(e, "sv_desc", descs, &d_desc, err))) return st;
+    if ((st = upload(e, "sv_desc", small_descs, &d_desc, err))) return st;
     if ((st = upload(e, "sv_idx", nz_idx, &d_idx, err))) return st;
     if ((st = upload(e, "sv_val", nz_val, &d_val, err))) return st;
     if ((st = ensure(e, "sv_work", sizeof(uint64_t) * work, (void **)&d_work, err))) return st;
     if ((st = ensure(e, "sv_out", sizeof(uint64_t) * outw, (void **)&d_out, err))) return st;
     if ((st = ensure(e, "sv_piv", sizeof(int32_t) * npiv, (void **)&d_piv, err))) return st;
     if ((st = ensure(e, "sv_rank", sizeof(int32_t) * count, (void **)&d_rank, err))) return st;
+    if ((st = ensure(e, "sv_state", sizeof(SolveState), (void **)&d_state, err))) return st;
     const size_t smem = (size_t)maxW * sizeof(uint64_t);
     CUDA_TRY(cudaFuncSetAttribute((const void *)k_right_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute((const void *)k_ri_elim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_right_inverse, kSolveThreads, smem));
-    const int grid = (int)std::min<uint64_t>(count, (uint64_t)e->sms * std::max(per_sm, 1));
     cudaEvent_t ev[2];
     CUDA_TRY(cudaEventCreate(&ev[0]));
     CUDA_TRY(cudaEventCreate(&ev[1]));
     cudaEventRecord(ev[0], e->stream);
-    k_right_inverse<<<grid, kSolveThreads, smem, e->stream>>>(d_desc, count, d_idx, d_val, d_work, d_out, d_piv, d_rank);
-    cudaError_t le = cudaGetLastError();
-    cudaEventRecord(ev[1], e->stream);
+    cudaError_t le = cudaSuccess;
+    if (!small_of.empty()) {
+        const int grid = (int)std::min<uint64_t>(small_of.size(), (uint64_t)e->sms * std::max(per_sm, 1));
+        k_right_inverse<<<grid, kSolveThreads, smem, e->stream>>>(d_desc, (uint32_t)small_of.size(), d_idx, d_val,
+                                                                  d_work, d_out, d_piv, d_rank);
+        le = cudaGetLastError();
+    }
+    for (size_t b = 0; b < big_of.size() && le == cudaSuccess; b++) {
+        const SolveDesc &D = descs[big_of[b]];
+        const size_t words = (size_t)D.R * D.W;
+        const unsigned fill_grid = (unsigned)std::min<size_t>((words + 1023) / 1024, (size_t)e->sms * 8);
+        const size_t esmem = (size_t)D.W * sizeof(uint64_t);
+        int elim_per_sm = 0;
+        le = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&elim_per_sm, (const void *)k_ri_elim, kSolveThreads, esmem);
+        if (le != cudaSuccess) break;
+        const unsigned elim_grid = (unsigned)std::min<int64_t>((D.R + 15) / 16, (int64_t)e->sms * std::max(elim_per_sm, 1));
+        k_ri_init<<<fill_grid, 1024, 0, e->stream>>>(D, d_idx, d_val, d_work, d_state);
+        if (D.nnz) k_ri_scatter<<<(D.nnz + 1023) / 1024, 1024, 0, e->stream>>>(D, d_idx, d_val, d_work);
+        for (uint32_t c = 0; c < D.C; c++) {
+            k_ri_pivot<<<1, 1024, 0, e->stream>>>(D, (int)c, d_work, d_piv, d_state);
+            k_ri_elim<<<elim_grid, kSolveThreads, esmem, e->stream>>>(D, (int)c, d_work, d_state);
+        }
+        k_ri_out<<<(unsigned)e->sms * 4, 256, 0, e->stream>>>(D, d_work, d_out, d_state, d_rank + small_of.size() + b);
+        le = cudaGetLastError();
+    }
+    if (le == cudaSuccess) le = cudaEventRecord(ev[1], e->stream);
     std::vector<uint64_t> out(outw);
-    std::vector<int32_t> piv(npiv), rank(count);
+    std::vector<int32_t> piv(npiv), rank_dev(count);
     if (le == cudaSuccess) {
         le = cudaMemcpyAsync(out.data(), d_out, sizeof(uint64_t) * outw, cudaMemcpyDeviceToHost, e->stream);
         if (le == cudaSuccess) le = cudaMemcpyAsync(piv.data(), d_piv, sizeof(int32_t) * npiv, cudaMemcpyDeviceToHost, e->stream);
-        if (le == cudaSuccess) le = cudaMemcpyAsync(rank.data(), d_rank, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, e->stream);
+        if (le == cudaSuccess) le = cudaMemcpyAsync(rank_dev.data(), d_rank, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, e->stream);
         if (le == cudaSuccess) le = cudaStreamSynchronize(e->stream);
     }
     float ms = 0;
@@ -1438,6 +1477,9 @@ zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, c
     cudaEventDestroy(ev[1]);
     CUDA_TRY(le);
     if (ms_device) *ms_device = ms;
+    std::vector<int32_t> rank(count);
+    for (size_t i = 0; i < small_of.size(); i++) rank[small_of[i]] = rank_dev[i];
+    for (size_t b = 0; b < big_of.size(); b++) rank[big_of[b]] = rank_dev[small_of.size() + b];
     for (uint32_t t = 0; t < count; t++) {
         SolveJob &J = *mine[t];
         const SolveDesc &d = descs[t];
@@ -1465,8 +1507,8 @@ static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err
     uint64_t nl = 0;
     CUDA_TRY(cudaSetDevice(e->device));
     const int s = (int)X.s, b = (int)X.b, nv = (int)X.nv;
-    if (s < 1 || s > 4096 || b < 1 || b > 32 || X.q >= ((uint64_t)1 << 56) || X.sec.empty()) {
-        err = "whole-GPU executor: needs s <= 4096, b <= 32, q < 2^56";
+    if (s < 1 || s > 4096 || b < 1 || b > 64 || X.q >= ((uint64_t)1 << 56) || X.sec.empty()) {
+        err = "whole-GPU executor: needs s <= 4096, b <= 64, q < 2^56";
         return ZETA_ERR_UNSUPPORTED;
     }
     zeta_status st = upload_binom(e, err);
@@ -1519,10 +1561,10 @@ static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err
         for (uint32_t ei = P.phase_begin[ph]; ei < P.phase_begin[ph + 1] && le == cudaSuccess; ei++) {
             const PlanEntry &E = P.entries[ei];
             LgCols cm;
-            for (int t = 0; t < 32; t++) cm.col[t] = cm.lc[t] = -1;
+            for (int t = 0; t < 64; t++) cm.col[t] = cm.lc[t] = -1;
             cm.c = 0;
             for (int col = 0; col < b; col++)
-                if (E.live >> col & 1u) {
+                if (E.live >> col & 1ull) {
                     cm.lc[col] = cm.c;
                     cm.col[cm.c++] = col;
                 }

@@ -2,7 +2,8 @@
 // after the plan structures): one instance at a time, the host walking its
 // plan (phases, entries, chunks) and every kernel spread over all SMs.  Built
 // for the cubic fourfolds (s = C(15, 5) = 3003, whose M(y) and A take 72 MB
-// each), it runs any instance with q < 2^56 and s <= 4096.
+// each) and for bases of more than 32 columns (quintic surfaces: b = 52), it
+// runs any instance with q < 2^56, s <= 4096 and b <= 64.
 //
 // Layouts (global memory): M, A row-major [r s + j] (Montgomery form, R = 2^64;
 // 32-bit words when q < 2^32, so that M and A of a cubic fourfold, 36 MB each,
@@ -24,8 +25,8 @@ struct LgVec {
 };
 
 struct LgCols {
-    int32_t col[32];  // basis column of live column lc
-    int32_t lc[32];   // live column of basis column col, or -1
+    int32_t col[64];  // basis column of live column lc
+    int32_t lc[64];   // live column of basis column col, or -1
     int32_t c;
 };
 
@@ -222,7 +223,7 @@ __global__ void k_lg_terms(int ws, LgCols cm, const Term *__restrict__ terms, ui
     const uint32_t t = begin + blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= end) return;
     const Term tm = terms[t];
-    const int lc = tm.col < 32 ? cm.lc[tm.col] : -1;
+    const int lc = tm.col < 64 ? cm.lc[tm.col] : -1;
     if (lc < 0) return;  // a term always lands on a live column of its entry
     uint64_t &w = W[(size_t)lc * ws + tm.row];
     w = addmod(w, tm.coeff, q);

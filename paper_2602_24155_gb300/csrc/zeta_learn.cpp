@@ -154,15 +154,15 @@ int others_at(const Instance &X, int t, const int32_t *W, uint64_t own) {
 
 // Share of the term's columns (live) that other terms of the reference game carry to W at level t - 1: the
 // columns a merge there would save (the term's own contribution is not counted when W is its own destination).
-float overlap_at(const Instance &X, int t, const int32_t *W, uint64_t own, uint32_t live) {
+float overlap_at(const Instance &X, int t, const int32_t *W, uint64_t own, uint64_t live) {
     if (!live || t - 1 < 1 || t - 1 >= (int)X.ref_cols.size()) return 0.f;
     const uint64_t key = pack(W, (int)X.nv);
     auto it = X.ref_cols[t - 1].find(key);
     if (it == X.ref_cols[t - 1].end()) return 0.f;
     int shared = 0;
-    for (int col = 0; col < 32; col++)
-        if ((live >> col & 1u) && (int)it->second[col] - (key == own ? 1 : 0) > 0) shared++;
-    return (float)shared / (float)__builtin_popcount(live);
+    for (int col = 0; col < 64; col++)
+        if ((live >> col & 1ull) && (int)it->second[col] - (key == own ? 1 : 0) > 0) shared++;
+    return (float)shared / (float)__builtin_popcountll(live);
 }
 
 }  // namespace
@@ -232,11 +232,11 @@ zeta_status reference_contributions(Instance &X) {
     const int tmax = nph;  // phase i plays level tmax - i
     X.ref_contrib.assign(tmax + 1, {});
     X.ref_cols.assign(tmax + 1, {});
-    auto add = [&](int t, uint64_t key, uint32_t live) {
+    auto add = [&](int t, uint64_t key, uint64_t live) {
         X.ref_contrib[t][key] += 1;
         auto &cnt = X.ref_cols[t][key];
-        for (int col = 0; col < 32; col++)
-            if (live >> col & 1u) cnt[col]++;
+        for (int col = 0; col < 64; col++)
+            if (live >> col & 1ull) cnt[col]++;
     };
     for (int ph = 0; ph + 1 < nph; ph++) {
         const int tn = tmax - ph - 1;  // next level
@@ -246,8 +246,8 @@ zeta_status reference_contributions(Instance &X) {
             const uint64_t key = pack(E.U, nv);
             if (E.start_chain >= 0) {
                 const Chain &C = X.chains[E.start_chain];
-                uint32_t live = 0;
-                for (uint32_t t = C.term_begin; t < C.term_end; t++) live |= 1u << X.terms[t].col;
+                uint64_t live = 0;
+                for (uint32_t t = C.term_begin; t < C.term_end; t++) live |= 1ull << X.terms[t].col;
                 add(tn, key, live);
             }
             if (E.arrival >= 0) {
@@ -274,7 +274,7 @@ zeta_status policy_dataset(Instance &X, std::vector<float> &feat, std::vector<ui
     auto cost = [](const Plan &P) { return (int64_t)P.column_steps + (int64_t)kChunkCost * (int64_t)P.chunks_played; };
     struct Dec {
         int t, left;
-        uint32_t live;
+        uint64_t live;
         std::array<int32_t, kMaxVars> U;
     };
     // 1. the cover game with Algorithm 3; its decisions (a term's first call may come from the level's search,

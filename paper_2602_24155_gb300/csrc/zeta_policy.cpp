@@ -76,7 +76,7 @@ uint64_t pack(const int32_t *U, int nv) {
 // first (optional): direction of the first chunk instead of Algorithm 3.
 // choose (optional): proposes the direction of a chunk (U, steps left) instead of Algorithm 3.
 template <typename Stop>
-void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_steps,
+void play_chunks(Instance &X, int32_t *U, uint64_t live, Stop stop, int max_steps,
                  const std::function<bool(const int32_t *, int, int *)> &choose = nullptr) {
     const int nv = (int)X.nv, base = (int)X.base, d = (int)X.d;
     int left = max_steps;
@@ -95,8 +95,8 @@ void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_step
         left -= k;
         X.plan.chunks_played++;
         X.plan.steps += k;
-        X.plan.column_steps += (uint64_t)k * __builtin_popcount(live);
-        X.plan.work += (uint64_t)k * __builtin_popcount(live) * X.s * X.s;
+        X.plan.column_steps += (uint64_t)k * __builtin_popcountll(live);
+        X.plan.work += (uint64_t)k * __builtin_popcountll(live) * X.s * X.s;
     }
 }
 
@@ -106,7 +106,7 @@ void play_chunks(Instance &X, int32_t *U, uint32_t live, Stop stop, int max_step
 // consecutive steps form one chunk.  Every step is legal: the coordinates in S
 // stay >= 1 until the last step (the condition of Prop. 3.3 holds) and the
 // pole order stays >= n.
-void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live) {
+void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint64_t live) {
     const int nv = (int)X.nv, x = (int)X.d - (int)X.base - 1;
     int inS[kMaxVars];
     for (int t = 0; t < nv; t++) inS[t] = (int)((X.Smask >> t) & 1u);
@@ -125,8 +125,8 @@ void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live
         for (int t = 0; t < nv; t++) U[t] -= run * prev[t];
         X.plan.chunks_played++;
         X.plan.steps += run;
-        X.plan.column_steps += (uint64_t)run * __builtin_popcount(live);
-        X.plan.work += (uint64_t)run * __builtin_popcount(live) * X.s * X.s;
+        X.plan.column_steps += (uint64_t)run * __builtin_popcountll(live);
+        X.plan.work += (uint64_t)run * __builtin_popcountll(live) * X.s * X.s;
         run = 0;
     };
     for (int j = 0; j < L; j++) {
@@ -149,9 +149,9 @@ void path_chunks(Instance &X, int32_t *U, const int32_t *V, int L, uint32_t live
     flush();
 }
 
-uint32_t chain_live(const Instance &X, const Chain &ch) {
-    uint32_t m = 0;
-    for (uint32_t t = ch.term_begin; t < ch.term_end; t++) m |= 1u << X.terms[t].col;
+uint64_t chain_live(const Instance &X, const Chain &ch) {
+    uint64_t m = 0;
+    for (uint32_t t = ch.term_begin; t < ch.term_end; t++) m |= 1ull << X.terms[t].col;
     return m;
 }
 
@@ -189,7 +189,7 @@ std::vector<std::vector<int32_t>> cover_destinations(
     //    next level's start terms and the destinations of this level's other terms (Algorithm 3, or the
     //    network's directions under the learned policy)
     std::vector<std::array<int32_t, kMaxVars>> fixedV;
-    std::vector<uint32_t> fixedLive;
+    std::vector<uint64_t> fixedLive;
     for (int c : next_starts) {
         std::array<int32_t, kMaxVars> V{};
         for (int t = 0; t < nv; t++) V[t] = X.chains[c].U[t];
@@ -227,7 +227,7 @@ std::vector<std::vector<int32_t>> cover_destinations(
             bool dom = true;
             for (int t = 0; t < nv && dom; t++) dom = fixedV[f][t] <= box[i][t];
             if (!dom) continue;
-            const int ov = __builtin_popcount(fixedLive[f] & e.live);
+            const int ov = __builtin_popcountll(fixedLive[f] & e.live);
             if (ov > best_overlap) { best_overlap = ov; best = (int)f; }
         }
         if (best >= 0) out[i].assign(fixedV[best].begin(), fixedV[best].end());
@@ -299,7 +299,7 @@ std::vector<std::vector<int32_t>> cover_destinations(
 zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     Plan &P = X.plan;
     P = Plan();
-    if (X.b > 32) { X.error = "more than 32 basis columns"; return X.status = ZETA_ERR_UNSUPPORTED; }
+    if (X.b > 64) { X.error = "more than 64 basis columns"; return X.status = ZETA_ERR_UNSUPPORTED; }
     const int nv = (int)X.nv, n = (int)X.n, d = (int)X.d, p = (int)X.p, base = (int)X.base;
     if (X.Smask != (1u << nv) - 1 && (policy == ZETA_POLICY_LEARNED || X.hook)) {
         X.error = "the learned policy takes S = {0..n} only";
@@ -336,7 +336,7 @@ zeta_status schedule_policy(Instance &X, zeta_policy policy) {
     }
 
     // phases with merging.  `cur` maps exponent -> (arrival block, live mask).
-    struct Arr { int32_t block; uint32_t live; };
+    struct Arr { int32_t block; uint64_t live; };
     std::unordered_map<uint64_t, Arr> cur, nxt;
     std::vector<std::vector<int32_t>> curU, nxtU;  // exponents of arrival blocks by index
     auto phase = [&](const std::vector<int> &starts, auto stop_for, auto max_steps,

@@ -14,10 +14,11 @@ import numpy as np
 from . import zeta_mlp_init, zeta_mlp_train, zeta_policy_dataset, POLICY_FEATURES
 
 
-def build_dataset(specs, seed=0):
+def build_dataset(specs, seed=0, opt=None):
+    """opt: options of the instances' games (e.g. r=1 for a relative-precision-1 workload)."""
     Xs, offs, labs = [], [], []
     with ThreadPoolExecutor(max_workers=min(len(specs), os.cpu_count() or 1) or 1) as pool:
-        sets = list(pool.map(zeta_policy_dataset, specs))
+        sets = list(pool.map(lambda spec: zeta_policy_dataset(spec, **(opt or {})), specs))
     for X, go, lab, _ in sets:
         for g in range(len(lab)):
             Xs.append(X[go[g]:go[g + 1]])
@@ -30,9 +31,9 @@ def build_dataset(specs, seed=0):
     return X.astype(np.float32), go, lab
 
 
-def train_policy(ctx, specs, hidden=64, epochs=30, batch_groups=512, lr=2e-3, seed=0):
+def train_policy(ctx, specs, hidden=64, epochs=30, batch_groups=512, lr=2e-3, seed=0, opt=None):
     """Returns (weights, final_loss, number of decisions)."""
-    X, go, lab = build_dataset(specs, seed)
+    X, go, lab = build_dataset(specs, seed, opt)
     w = zeta_mlp_init(hidden, seed)
     w, loss = zeta_mlp_train(ctx, hidden, w, X, go, lab, epochs, batch_groups, lr)
     return w, loss, len(lab)

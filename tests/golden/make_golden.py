@@ -1,13 +1,15 @@
 """Writes the stored expected values under tests/golden/ from the oracle alone.
 
-Run from the repository root:  python tests/golden/make_golden.py [k3 | threefold]
+Run from the repository root:  python tests/golden/make_golden.py [k3 | threefold | fourfold]
 Each value is produced by oracle/ (which the point-count and closed-form
 tests pin); nothing here touches the CUDA path.  `k3` writes the
 full-precision P(T) of three quartic K3 surfaces (tens of minutes of CPU per
 surface, one process each).  `threefold` writes P(T) of the dense cubic
 threefold over F_11 drawn with seed 11 (S = {4}) at series order N = 6, the
 least N whose columns reach the relative precision r = (5, 6) (about half an
-hour of CPU).
+hour of CPU).  `fourfold` writes #X(F_7) and #X(F_49) of a dense cubic
+fourfold (point counts, about ten minutes of CPU): its P(T) is beyond the
+oracle's reach (s = 3003), the counts fix a_1 and a_2.
 """
 import multiprocessing as mp
 import os
@@ -82,10 +84,35 @@ def threefold_main():
         fh.write("P: %s\n" % " ".join(map(str, res.P)))
 
 
+# dense_candidate(5, 3, 7, seed 5, instance i, attempt 0) for i = 0, 1, ...: about one draw in sixty is
+# {5}-smooth over F_7 (a common zero of the J_S generators may sit on any of 32 coordinate strata); instance 76 is
+# the first
+FOURFOLD_INSTANCE = 76
+
+
+def fourfold_main():
+    from oracle import pins
+    n, d, p = 5, 3, 7
+    c = zi.dense_candidate(n, d, p, 5, FOURFOLD_INSTANCE, 0)
+    assert cohomology.is_smooth(n, d, p, c)
+    t = time.time()
+    counts = [pins.count_points(n, d, p, c, r) for r in (1, 2)]
+    with open(os.path.join(HERE, "cubic_fourfold_f7.txt"), "w") as fh:
+        fh.write("# dense cubic fourfold over F_7 (zeta_inputs.dense_candidate seed 5, instance %d, attempt 0),\n"
+                 % FOURFOLD_INSTANCE)
+        fh.write("# smooth and {5}-smooth; #X(F_7^r) for r = 1, 2 by evaluating f on every point of P^5\n")
+        fh.write("n d p: %d %d %d\n" % (n, d, p))
+        fh.write("coeffs: %s\n" % " ".join(map(str, c)))
+        fh.write("oracle seconds: %.0f\n" % (time.time() - t))
+        fh.write("counts: %s\n" % " ".join(map(str, counts)))
+
+
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "k3":
         k3_main()
     elif len(sys.argv) > 1 and sys.argv[1] == "threefold":
         threefold_main()
+    elif len(sys.argv) > 1 and sys.argv[1] == "fourfold":
+        fourfold_main()
     else:
         main()

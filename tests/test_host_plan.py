@@ -490,3 +490,18 @@ def test_host_game_with_S_n_matches_the_oracle_game(case, policy):
                 assert e.status == 2
     g = z.zeta_plan((n, d, p, c), policy=policy, r=1, S=S)["game"]
     assert (g["chunks"], g["steps"], g["merges"]) == _oracle_game_counts(n, d, p, c, policy, S, 1)
+
+
+def test_quintic_surface_plans_with_52_columns():
+    """Quintic surfaces (b = 52 > 32): the host plans them with 64-bit column masks (relative precision 1, M = 3);
+    every term's columns are carried, and zeta_plan_moves, whose `live` export is one 32-bit word, refuses them."""
+    spec = (3, 5, 7, zi.fermat(3, 5))
+    P = z.zeta_plan(spec, r=1, policy="p_chunk")
+    assert P["b"] == 52 and P["s"] == 455 and P["M"] == 3
+    g = P["game"]
+    assert g["chunks"] > 0 and g["column_steps"] >= g["steps"]
+    assert set(int(c) for c in P["term_rc"][:, 1]) <= set(range(52))
+    assert max(int(c) for c in P["term_rc"][:, 1]) >= 32
+    with pytest.raises(z.ZetaError) as e:
+        z.zeta_plan_moves(spec, r=1, policy="p_chunk")
+    assert e.value.status == 3
