@@ -381,7 +381,7 @@ def _quintic_surfaces(z, ctx, stream, torch, count, train_count):
     return out
 
 
-def _cubic_fourfolds(z, ctx, stream, torch, dense):
+def _cubic_fourfolds(z, ctx, stream, torch, dense, N=0):
     """Cubic fourfolds over F_7 (n = 5, d = 3: s = C(15, 5) = 3003, b = 22, S = {5}) at relative precision 1 (M = 9;
     the full precision needs 7^25, beyond 64-bit residues) on the whole-GPU executor: the Fermat cubic fourfold and,
     with `dense`, the dense one of tests/golden/cubic_fourfold_f7.txt (dense_candidate seed 5, instance 76).  The
@@ -395,14 +395,14 @@ def _cubic_fourfolds(z, ctx, stream, torch, dense):
     for name, c in cases:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        P, per, tot = z.zeta_batch(ctx, [(5, 3, 7, c)], policy="p_chunk", r=1)
+        P, per, tot = z.zeta_batch(ctx, [(5, 3, 7, c)], policy="p_chunk", r=1, **({"N": N, "y_only": True} if N else {}))
         wall = time.perf_counter() - t0
         out[name] = {"status": per[0]["status"], "wall_s": wall, "ms_host_setup": tot["ms_host_setup"],
                      "ms_kernel": tot["ms_kernel"], "kernel_launches": tot["kernel_launches"],
                      "chunks": tot["chunks"], "steps": tot["steps"], "column_steps": tot["column_steps"],
                      "column_steps_per_s": tot["column_steps"] / (tot["ms_kernel"] / 1000.0),
                      "modmac_per_s": tot["column_steps"] * 3003.0 * 3003.0 / (tot["ms_kernel"] / 1000.0),
-                     "height": fourfold_height(P[0], 7) if P[0] else None}
+                     "height": fourfold_height(P[0], 7) if P[0] and not N else None}
     return out
 
 
@@ -481,6 +481,10 @@ def main():
                     help="truncate the K3 line's series orders to N (small profiling case; 0 = full precision)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed stream")
     ap.add_argument("--no-fourfold", action="store_true", help="skip the cubic fourfold line (Fermat, r = 1)")
+    ap.add_argument("--only", default=None, choices=["fourfold", "surfaces"],
+                    help="run only this line (profiling a small case of its kernels) and print it")
+    ap.add_argument("--fourfold-N", type=int, default=0,
+                    help="series order override of the --only fourfold run (a small case; 0 = the rule)")
     ap.add_argument("--fourfold-dense", action="store_true",
                     help="add the dense cubic fourfold to the fourfold line (several minutes)")
     ap.add_argument("--surface-count", type=int, default=256,
@@ -504,6 +508,15 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
     ctx = z.zeta_create(local, stream.cuda_stream)
+    if args.only == "fourfold":
+        print(json.dumps({"cubic_fourfolds": _cubic_fourfolds(z, ctx, stream, torch, args.fourfold_dense,
+                                                              args.fourfold_N)}))
+        z.zeta_destroy(ctx)
+        return
+    if args.only == "surfaces":
+        print(json.dumps({"quintic_surfaces": _quintic_surfaces(z, ctx, stream, torch, args.surface_count, 24)}))
+        z.zeta_destroy(ctx)
+        return
     specs = _instances_lib(rank, args.count, z)
     opt = dict(policy=args.policy, path=args.path)
     learned = None

@@ -96,7 +96,12 @@ typedef struct {
      * library's documentation).  r_override sets the relative precision r;
      * N_override[m-1] sets the series order N_m.  With overrides smaller
      * than the rules the Frobenius matrix is a truncation and P(T) is not
-     * the zeta function; used for small parity cases. */
+     * the zeta function; used for small parity cases.  With r_override = r
+     * alone, a_i is determined mod p^(r + H(i)), H the Hodge polygon (the
+     * slopes n - m of the basis elements of pole order m in increasing
+     * order), and mod at most the largest power of p below 2^63: what the
+     * Newton height and the unit roots need (relative precision 1 for the
+     * height of a cubic fourfold, the unit roots of a quintic surface). */
     uint32_t r_override;
     uint32_t N_override[8];
     uint32_t flags;             /* ZETA_FLAG_* bits */

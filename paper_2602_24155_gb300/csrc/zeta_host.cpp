@@ -897,23 +897,25 @@ zeta_status finish_instance(Instance &X) {
     std::vector<int> e = coefficient_digits((int)n, p, (int)b);
     int K = 0;
     for (uint32_t i = 0; i <= b / 2; i++) K = std::max(K, e[i]);
-    uint64_t pK;
-    if (!pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK)) {
-        // a run below the precision rule (relative precision rmin) knows a_i only mod p^(rmin + H(i)), H the
-        // Hodge polygon (the slopes n - m of the basis elements in increasing order): the charpoly is then
-        // taken mod the largest power of p below 2^63 when that power covers those digits
+    // a run below the precision rule (relative precision rmin) knows some a_i only mod p^(rmin + H(i)) with
+    // rmin + H(i) < e_i, H the Hodge polygon of the slopes n - m of the basis elements in increasing order
+    bool truncated_run = false;
+    {
         std::vector<int> slope;
         for (uint32_t col = 0; col < b; col++) slope.push_back((int)n - (int)X.pole[col]);
         std::sort(slope.begin(), slope.end());
-        int need = 0, H = 0;
-        for (uint32_t i = 1; i <= b / 2; i++) {
-            H += slope[i - 1];
-            need = std::max(need, std::min(e[i], (int)rmin + H));
+        for (uint32_t i = 1, H = 0; i <= b / 2; i++) {
+            H += (uint32_t)slope[i - 1];
+            if ((int)(rmin + H) < e[i]) truncated_run = true;
         }
-        int Kfit = 0;
-        while (pow_fits(p, (uint32_t)Kfit + 1, (uint64_t)1 << 63, &pK)) Kfit++;
-        if (need > Kfit) { X.error = "charpoly precision exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
-        K = Kfit;
+    }
+    uint64_t pK;
+    if (!pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK)) {
+        // a truncated run takes the charpoly mod the largest power p^K below 2^63: a_i is then known mod
+        // p^min(rmin + H(i), K); a run at the rule's precision needs every digit
+        if (!truncated_run) { X.error = "charpoly precision exceeds 2^63"; return X.status = ZETA_ERR_PRECISION; }
+        K = 0;
+        while (pow_fits(p, (uint32_t)K + 1, (uint64_t)1 << 63, &pK)) K++;
         for (auto &x : e) x = std::min(x, K);
         pow_fits(p, (uint32_t)K, (uint64_t)1 << 63, &pK);
     }
@@ -935,13 +937,32 @@ zeta_status finish_instance(Instance &X) {
         uint64_t x = cp[i] % mod;
         X.P[i] = (x > mod / 2) ? (i128)x - (i128)mod : (i128)x;
     }
+    // a_{b-i} = eps p^(w(b-2i)/2) a_i (functional equation, weight w = n - 1): exact while it fits 125 bits; a
+    // truncated run whose exact value would not (quintic surfaces: 11^52) gets it mod p^K like its other digits
     int w = (int)n - 1;
+    const u128 limit = (u128)1 << 125;
     for (uint32_t i = 0; i < (b + 1) / 2; i++) {
         uint32_t j = b - i;
         if (j <= b / 2) continue;
-        i128 pw = 1;
-        for (int t = 0; t < w * ((int)b - 2 * (int)i) / 2; t++) pw *= p;
-        X.P[j] = (i128)X.eps * pw * X.P[i];
+        const int ex = w * ((int)b - 2 * (int)i) / 2;
+        const u128 mag = (u128)(X.P[i] < 0 ? -X.P[i] : X.P[i]);
+        u128 pw = 1;
+        bool fits = true;
+        for (int t = 0; t < ex && fits; t++) {
+            pw *= p;
+            if (pw > limit / (mag ? mag : 1)) fits = false;
+        }
+        if (fits) {
+            X.P[j] = (i128)X.eps * (i128)pw * X.P[i];
+            continue;
+        }
+        if (!truncated_run) { X.error = "P(T) coefficient exceeds 125 bits"; return X.status = ZETA_ERR_PRECISION; }
+        uint64_t pe = 1 % pK;
+        for (int t = 0; t < ex; t++) pe = (uint64_t)((u128)pe * p % pK);
+        const uint64_t ai = (uint64_t)(((X.P[i] % (i128)pK) + (i128)pK) % (i128)pK);
+        uint64_t x = (uint64_t)((u128)pe * ai % pK);
+        if (X.eps < 0 && x) x = pK - x;
+        X.P[j] = (x > pK / 2) ? (i128)x - (i128)pK : (i128)x;
     }
     X.ms_finish = now_ms() - t0;
     return ZETA_OK;

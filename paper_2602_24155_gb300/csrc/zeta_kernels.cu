@@ -1616,12 +1616,19 @@ static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err
                         uint64_t *Vg = V + (size_t)c0 * sp;
                         nl++;
                         if constexpr (NARROW) {
-                            const uint32_t *Mn = (const uint32_t *)d_M, *An = (const uint32_t *)d_A;
+                            // chunks with one or two columns: M(k-1) - tA on the fly; wider ones: M <- M - A
+                            uint32_t *Mn = (uint32_t *)d_M;
+                            const uint32_t *An = (const uint32_t *)d_A;
                             const uint64_t t = tR[y];
-                            if (cg == 1) k_lg_step_narrow<1><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
-                            else if (cg == 2) k_lg_step_narrow<2><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
-                            else if (cg <= 4) k_lg_step_narrow<4><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
-                            else k_lg_step_narrow<8><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t);
+                            const int last = c0 + kLgMaxCpt >= cm.c;
+                            if (cm.c <= 2) {
+                                if (cg == 1) k_lg_step_narrow<1, false><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t, 0);
+                                else k_lg_step_narrow<2, false><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, t, 0);
+                            } else if (cg <= 4) {
+                                k_lg_step_narrow<4, true><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, 0, last);
+                            } else {
+                                k_lg_step_narrow<8, true><<<step_grid, kLgWarps * 32, 0, stream>>>(s, sp, cg, Wg, Vg, Mn, An, Q, 0, last);
+                            }
                         } else {
                             const int last = c0 + kLgMaxCpt >= cm.c;
                             if (cg == 1) k_lg_step<1, T><<<step_grid, kLgWarps * 32, 0, stream>>>(s, cg, Wg, Vg, d_M, d_A, Q, last);

@@ -61,15 +61,23 @@ __global__ void __launch_bounds__(256) k_lg_gen(int s, int nv, uint32_t sec_cols
     const int col = colidx[j];
     uint64_t aL = 0, mL = 0, mH = 0;
     if (col >= 0) {
-        for (int i = 0; i < nv; i++) {
-            const int row = secrow[i * s + r];
-            if (row < 0) continue;
-            const uint64_t val = (uint64_t)__ldg(&Sec[(size_t)row * sec_cols + col]);
-            aL += val * (uint64_t)v.x[i];  // < d q < 2^63
-            const uint64_t wm = (uint64_t)(U.x[i] - v.x[i] + monoS[r * nv + i]);
-            add128(mL, mH, val * wm);
-            mH += mul_hi64(val, wm);
+        uint64_t val[kMaxVars];  // all section reads in flight before the first is used
+#pragma unroll
+        for (int i = 0; i < kMaxVars; i++) {
+            val[i] = 0;
+            if (i < nv) {
+                const int row = secrow[i * s + r];
+                if (row >= 0) val[i] = (uint64_t)__ldg(&Sec[(size_t)row * sec_cols + col]);
+            }
         }
+#pragma unroll
+        for (int i = 0; i < kMaxVars; i++)
+            if (i < nv) {
+                aL += val[i] * (uint64_t)v.x[i];  // < d q < 2^63
+                const uint64_t wm = (uint64_t)(U.x[i] - v.x[i] + monoS[r * nv + i]);
+                add128(mL, mH, val[i] * wm);
+                mH += mul_hi64(val[i], wm);
+            }
     }
     while (aL >= Q.q) aL -= Q.q;
     A[e] = (T)aL;
@@ -132,8 +140,7 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step(int s, int c, const u
 
 // Narrow moduli (q < 2^26: the cubic fourfolds at relative precision 1, q = 7^9): products of two residues are
 // below 2^52, so a 64-bit sum of up to 4096 of them needs no limbs -- one mad.wide.u32 per product.  M and A
-// are 32-bit words in rows of stride sp (s rounded up to 4, the padding zero), read 16 bytes at a time, and M
-// is not written back: the t-th step of a chunk applies M(k-1-t) = M(k-1) - t A as M(k-1) W - t (A W).
+// are 32-bit words in rows of stride sp (s rounded up to 4, the padding zero), read 16 bytes at a time.
 
 // A R and M(k-1) R as above, from Sec R^2 mod q (32-bit words): each is one REDC of a sum below 2^48.
 __global__ void __launch_bounds__(256) k_lg_gen_narrow(int s, int sp, int nv, uint32_t sec_cols,
@@ -148,61 +155,97 @@ __global__ void __launch_bounds__(256) k_lg_gen_narrow(int s, int sp, int nv, ui
     uint64_t aL = 0, mL = 0;
     const int col = j < s ? colidx[j] : -1;
     if (col >= 0) {
-        for (int i = 0; i < nv; i++) {
-            const int row = secrow[i * s + r];
-            if (row < 0) continue;
-            const uint64_t val = __ldg(&SecRR[(size_t)row * sec_cols + col]);
-            aL += val * (uint64_t)v.x[i];
-            mL += val * (uint64_t)(U.x[i] - v.x[i] + monoS[r * nv + i]);
+        // every section read issued before the first is used (the reads are independent; issued one after the
+        // other the kernel waits nv memory latencies per entry)
+        uint32_t val[kMaxVars];
+#pragma unroll
+        for (int i = 0; i < kMaxVars; i++) {
+            val[i] = 0;
+            if (i < nv) {
+                const int row = secrow[i * s + r];
+                if (row >= 0) val[i] = __ldg(&SecRR[(size_t)row * sec_cols + col]);
+            }
         }
+#pragma unroll
+        for (int i = 0; i < kMaxVars; i++)
+            if (i < nv) {
+                aL += (uint64_t)val[i] * (uint64_t)v.x[i];
+                mL += (uint64_t)val[i] * (uint64_t)(U.x[i] - v.x[i] + monoS[r * nv + i]);
+            }
     }
     A[e] = (uint32_t)redc(aL, 0, Q);
     M[e] = (uint32_t)redc(mL, 0, Q);
 }
 
-// Step t of a chunk for columns [0, c) (c <= CPT): V = M(k-1) W - t (A W), tR = t R mod q.  One warp per row,
-// each lane four consecutive j per load.  W, V: 64-bit words, column stride sp.
-template <int CPT>
+// Step t of a chunk for columns [0, c) (c <= CPT).  One warp per row, each lane four consecutive j per 16-byte
+// load; W staged in shared memory as 32-bit words, kLgTileJ columns j at a time.  W, V: 64-bit words, column
+// stride sp.  Two forms:
+//  WRITE = false: V = M(k-1) W - t (A W), tR = t R mod q; M is only read (two products per entry: chunks with one
+//                 or two columns, where the step is bound by reading M and A);
+//  WRITE = true:  V = M W with the current M(k-1-t), and, when `last`, M <- M - A (one product per entry: chunks
+//                 with three or more columns, where the products dominate).
+constexpr int kLgTileJ = 1024;
+
+template <int CPT, bool WRITE>
 __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp, int c, const uint64_t *__restrict__ W,
-                                                                  uint64_t *__restrict__ V,
-                                                                  const uint32_t *__restrict__ M,
-                                                                  const uint32_t *__restrict__ A, ModQ Q, uint64_t tR) {
+                                                                  uint64_t *__restrict__ V, uint32_t *__restrict__ M,
+                                                                  const uint32_t *__restrict__ A, ModQ Q, uint64_t tR,
+                                                                  int last) {
+    __shared__ __align__(16) uint32_t sW[CPT][kLgTileJ];
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * kLgWarps + (threadIdx.x >> 5);
-    if (r >= s) return;  // the whole warp leaves together
+    const bool row_ok = r < s;  // a warp past the last row still helps stage W
     uint64_t SM[CPT], SA[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; t++) SM[t] = SA[t] = 0;
-    const uint4 *Mr = reinterpret_cast<const uint4 *>(M + (size_t)r * sp);
-    const uint4 *Ar = reinterpret_cast<const uint4 *>(A + (size_t)r * sp);
-    const int n4 = sp >> 2;
+    uint4 *Mr = reinterpret_cast<uint4 *>(M + (size_t)(row_ok ? r : 0) * sp);
+    const uint4 *Ar = reinterpret_cast<const uint4 *>(A + (size_t)(row_ok ? r : 0) * sp);
+    for (int j0 = 0; j0 < sp; j0 += kLgTileJ) {
+        const int jn = min(kLgTileJ, sp - j0);  // a multiple of 4
+        __syncthreads();  // the previous tile is consumed
+        for (int e = threadIdx.x; e < c * jn; e += kLgWarps * 32) {
+            const int t = e / jn, j = e - t * jn;
+            sW[t][j] = (uint32_t)W[(size_t)t * sp + j0 + j];
+        }
+        __syncthreads();
+        if (row_ok) {
 #pragma unroll 2
-    for (int q4 = lane; q4 < n4; q4 += 32) {
-        const uint4 m = __ldg(&Mr[q4]);
-        const uint4 a = __ldg(&Ar[q4]);
+            for (int q4 = lane; q4 < (jn >> 2); q4 += 32) {
+                const int g = (j0 >> 2) + q4;
+                const uint4 m = Mr[g];
+                uint4 a = make_uint4(0, 0, 0, 0);
+                if (!WRITE || last) a = __ldg(&Ar[g]);
 #pragma unroll
-        for (int t = 0; t < CPT; t++) {
-            if (t < c) {
-                const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(W + (size_t)t * sp + 4 * (size_t)q4);
-                const ulonglong2 w01 = __ldg(&w2[0]), w23 = __ldg(&w2[1]);
-                madw(SM[t], m.x, (uint32_t)w01.x);
-                madw(SM[t], m.y, (uint32_t)w01.y);
-                madw(SM[t], m.z, (uint32_t)w23.x);
-                madw(SM[t], m.w, (uint32_t)w23.y);
-                madw(SA[t], a.x, (uint32_t)w01.x);
-                madw(SA[t], a.y, (uint32_t)w01.y);
-                madw(SA[t], a.z, (uint32_t)w23.x);
-                madw(SA[t], a.w, (uint32_t)w23.y);
+                for (int t = 0; t < CPT; t++) {
+                    if (t < c) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(&sW[t][4 * q4]);
+                        madw(SM[t], m.x, w.x);
+                        madw(SM[t], m.y, w.y);
+                        madw(SM[t], m.z, w.z);
+                        madw(SM[t], m.w, w.w);
+                        if (!WRITE) {
+                            madw(SA[t], a.x, w.x);
+                            madw(SA[t], a.y, w.y);
+                            madw(SA[t], a.z, w.z);
+                            madw(SA[t], a.w, w.w);
+                        }
+                    }
+                }
+                if (WRITE && last)
+                    Mr[g] = make_uint4((uint32_t)submod(m.x, a.x, Q.q), (uint32_t)submod(m.y, a.y, Q.q),
+                                       (uint32_t)submod(m.z, a.z, Q.q), (uint32_t)submod(m.w, a.w, Q.q));
             }
         }
     }
+    if (!row_ok) return;
 #pragma unroll
     for (int t = 0; t < CPT; t++) {
         if (t >= c) break;
-        const uint64_t x = redc(SM[t], 0, Q);           // M W mod q
-        const uint64_t y = redc(SA[t], 0, Q);           // A W mod q
-        const uint64_t ty = redc(y * tR, mul_hi64(y, tR), Q);
-        uint64_t z = submod(x, ty, Q.q);
+        uint64_t z = redc(SM[t], 0, Q);  // M W mod q
+        if (!WRITE) {
+            const uint64_t y = redc(SA[t], 0, Q);  // A W mod q
+            z = submod(z, redc(y * tR, mul_hi64(y, tR), Q), Q.q);
+        }
 #pragma unroll
         for (int off = 16; off; off >>= 1) z = addmod(z, __shfl_xor_sync(0xffffffffu, z, off), Q.q);
         if (lane == 0) V[(size_t)t * sp + r] = z;
