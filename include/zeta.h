@@ -238,8 +238,10 @@ zeta_status zeta_batch(zeta_ctx *ctx, const zeta_hypersurface *hs, size_t count,
  *      of the start terms, sections and tables to device memory.  The plan
  *      owns that device memory until zeta_batch_release.
  *  zeta_batch_run: enqueue the recurrence kernels on the context's stream
- *      and return without waiting (inputs already resident).  May be called
- *      again on the same plan; each run recomputes the same numerators.
+ *      and return without waiting (inputs already resident); instances on
+ *      the whole-GPU executor (C(dn, n) > 512 or more than 32 basis columns)
+ *      run to completion before it returns.  May be called again on the same
+ *      plan; each run launches again and recomputes the same numerators.
  *  zeta_batch_finish: wait for the stream, read the numerators back, run
  *      the host finish; outputs as in zeta_batch.
  *  zeta_batch_release: free the plan (NULL allowed). */

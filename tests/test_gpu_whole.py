@@ -82,3 +82,20 @@ def test_fermat_cubic_fourfold_f7_relative_precision_one(ctx):
         mod = p ** (1 + H[i])
         assert (P[0][i] - exact[i]) % mod == 0, i
     assert fourfold_height(P[0], p) == 1
+
+
+def test_every_run_of_a_prepared_batch_launches_again(ctx):
+    """zeta_batch_run may be called again on a plan and runs the batch again each time (how the bench times
+    resident inputs): three runs of a batch holding a persistent-executor instance and a whole-GPU one give the
+    same P(T) as one, with three persistent launches."""
+    specs = [zi.draw_instance("quintic_curves", i, _accept)[:4] for i in (0, 1)]
+    specs.append((3, 5, 11, zi.fermat(3, 5)))          # b = 52: the whole-GPU executor
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", r=1)
+    plan.run()
+    P1, _, tot1 = plan.finish()
+    for _ in range(3):
+        plan.run()
+    P3, _, tot3 = plan.finish()
+    plan.release()
+    assert P1 == P3
+    assert tot3["kernel_launches"] > tot1["kernel_launches"] and tot3["ms_kernel"] > tot1["ms_kernel"]
