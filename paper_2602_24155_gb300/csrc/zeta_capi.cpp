@@ -194,18 +194,16 @@ struct zeta_batch_plan {
     bool launched = false, large_done = false;
 };
 
-// The instances of the whole-GPU executor, in plan order, after the persistent launch was enqueued.
+// The instances of the whole-GPU executor, after the persistent launch was enqueued.
 static zeta_status run_large(zeta_ctx *ctx, zeta_batch_plan *P) {
     if (P->large_done) return ZETA_OK;
     P->large_done = true;
-    for (Instance *X : P->large) {
-        double ms = 0;
-        uint64_t launches = 0;
-        zeta_status st = engine_run_large(ctx->engine, *X, ctx->error, &ms, &launches);
-        if (st) return st;
-        P->ms_large += ms;
-        P->large_launches += launches;
-    }
+    double ms = 0;
+    uint64_t launches = 0;
+    zeta_status st = engine_run_large(ctx->engine, P->large, ctx->error, &ms, &launches);
+    if (st) return st;
+    P->ms_large += ms;
+    P->large_launches += launches;
     return ZETA_OK;
 }
 

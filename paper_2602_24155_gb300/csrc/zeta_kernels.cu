@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -28,6 +29,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "zeta_internal.h"
@@ -717,17 +719,27 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// A lane of the whole-GPU executor: its own stream and buffers, so that several instances run at once, one host
+// thread each.  Slot 0 uses the engine's stream.
+struct LgSlot {
+    cudaStream_t stream = nullptr;
+    bool owned = false;
+    std::map<std::string, DevBuf> bufs;
+};
+
 struct DeviceEngine {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;  // second lane for pipelined sub-batches (non-blocking, created on first use)
     int sms = 0;
     std::map<std::string, DevBuf> bufs;
+    std::vector<LgSlot> lg;       // whole-GPU executor lanes (created on first use)
     bool binom_ready = false;
 };
 
-static zeta_status ensure(DeviceEngine *e, const char *name, size_t bytes, void **out, std::string &err) {
-    DevBuf &b = e->bufs[name];
+static zeta_status ensure_in(std::map<std::string, DevBuf> &bufs, const char *name, size_t bytes, void **out,
+                             std::string &err) {
+    DevBuf &b = bufs[name];
     if (b.bytes < bytes) {
         if (b.ptr) cudaFree(b.ptr);
         b.ptr = nullptr;
@@ -743,6 +755,10 @@ static zeta_status ensure(DeviceEngine *e, const char *name, size_t bytes, void 
     }
     *out = b.ptr;
     return ZETA_OK;
+}
+
+static zeta_status ensure(DeviceEngine *e, const char *name, size_t bytes, void **out, std::string &err) {
+    return ensure_in(e->bufs, name, bytes, out, err);
 }
 
 static ModQ make_modq(uint64_t q) {
@@ -784,6 +800,11 @@ void engine_destroy(DeviceEngine *e) {
     if (e->side) cudaStreamDestroy(e->side);
     for (auto &kv : e->bufs)
         if (kv.second.ptr) cudaFree(kv.second.ptr);
+    for (LgSlot &sl : e->lg) {
+        if (sl.owned && sl.stream) cudaStreamDestroy(sl.stream);
+        for (auto &kv : sl.bufs)
+            if (kv.second.ptr) cudaFree(kv.second.ptr);
+    }
     delete e;
 }
 
@@ -808,6 +829,16 @@ static zeta_status upload(DeviceEngine *e, const char *name, const std::vector<T
     zeta_status st = ensure(e, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p, err);
     if (st) return st;
     if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, e->stream));
+    *out = (T *)p;
+    return ZETA_OK;
+}
+
+template <typename T>
+static zeta_status upload_in(LgSlot &sl, const char *name, const std::vector<T> &v, T **out, std::string &err) {
+    void *p;
+    zeta_status st = ensure_in(sl.bufs, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p, err);
+    if (st) return st;
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, sl.stream));
     *out = (T *)p;
     return ZETA_OK;
 }
@@ -1501,7 +1532,8 @@ zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, c
 // per step (per group of eight columns), and the merge or the numerators.  Fills X.H; ms_device = the plan's
 // time between CUDA events on the stream.
 template <typename T, bool NARROW>
-static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err, double *ms_device, uint64_t *launches) {
+static zeta_status run_large_impl(DeviceEngine *e, LgSlot &slot, Instance &X, std::string &err, double *ms_device,
+                                  uint64_t *launches) {
     if (ms_device) *ms_device = 0;
     if (launches) *launches = 0;
     uint64_t nl = 0;
@@ -1525,22 +1557,22 @@ static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err
     uint64_t *d_W, *d_V, *d_H, *d_blocks;
     int32_t *d_monoS, *d_secrow, *d_colidx;
     Term *d_terms;
-    if ((st = upload(e, "lg_sec", secR, &d_sec, err))) return st;
+    if ((st = upload_in(slot, "lg_sec", secR, &d_sec, err))) return st;
     std::vector<T>().swap(secR);
-    if ((st = upload(e, "lg_monoS", X.tab_monoS, &d_monoS, err))) return st;
-    if ((st = upload(e, "lg_secrow", X.tab_secrow, &d_secrow, err))) return st;
-    if ((st = upload(e, "lg_terms", X.terms, &d_terms, err))) return st;
+    if ((st = upload_in(slot, "lg_monoS", X.tab_monoS, &d_monoS, err))) return st;
+    if ((st = upload_in(slot, "lg_secrow", X.tab_secrow, &d_secrow, err))) return st;
+    if ((st = upload_in(slot, "lg_terms", X.terms, &d_terms, err))) return st;
     const int sp = NARROW ? (s + 3) & ~3 : s;  // row stride of M and A, column stride of W and V
     const size_t ss = (size_t)s * sp, block_words = (size_t)s * b;
     const size_t cap = std::max<size_t>(X.plan.cap, 1);
-    if ((st = ensure(e, "lg_M", sizeof(T) * ss, (void **)&d_M, err))) return st;
-    if ((st = ensure(e, "lg_A", sizeof(T) * ss, (void **)&d_A, err))) return st;
-    if ((st = ensure(e, "lg_colidx", sizeof(int32_t) * s, (void **)&d_colidx, err))) return st;
-    if ((st = ensure(e, "lg_W", sizeof(uint64_t) * sp * b, (void **)&d_W, err))) return st;
-    if ((st = ensure(e, "lg_V", sizeof(uint64_t) * sp * b, (void **)&d_V, err))) return st;
-    if ((st = ensure(e, "lg_H", sizeof(uint64_t) * X.h_rows * b, (void **)&d_H, err))) return st;
-    if ((st = ensure(e, "lg_blocks", sizeof(uint64_t) * 2 * cap * block_words, (void **)&d_blocks, err))) return st;
-    cudaStream_t stream = e->stream;
+    if ((st = ensure_in(slot.bufs, "lg_M", sizeof(T) * ss, (void **)&d_M, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_A", sizeof(T) * ss, (void **)&d_A, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_colidx", sizeof(int32_t) * s, (void **)&d_colidx, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_W", sizeof(uint64_t) * sp * b, (void **)&d_W, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_V", sizeof(uint64_t) * sp * b, (void **)&d_V, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_H", sizeof(uint64_t) * X.h_rows * b, (void **)&d_H, err))) return st;
+    if ((st = ensure_in(slot.bufs, "lg_blocks", sizeof(uint64_t) * 2 * cap * block_words, (void **)&d_blocks, err))) return st;
+    cudaStream_t stream = slot.stream;
     CUDA_TRY(cudaMemsetAsync(d_H, 0, sizeof(uint64_t) * X.h_rows * b, stream));
     CUDA_TRY(cudaMemsetAsync(d_W, 0, sizeof(uint64_t) * sp * b, stream));  // the padding rows stay zero
     CUDA_TRY(cudaMemsetAsync(d_V, 0, sizeof(uint64_t) * sp * b, stream));
@@ -1671,10 +1703,86 @@ static zeta_status run_large_impl(DeviceEngine *e, Instance &X, std::string &err
     return ZETA_OK;
 }
 
-zeta_status engine_run_large(DeviceEngine *e, Instance &X, std::string &err, double *ms_device, uint64_t *launches) {
-    if (X.q < ((uint64_t)1 << 26)) return run_large_impl<uint32_t, true>(e, X, err, ms_device, launches);
-    return X.q < ((uint64_t)1 << 32) ? run_large_impl<uint32_t, false>(e, X, err, ms_device, launches)
-                                     : run_large_impl<uint64_t, false>(e, X, err, ms_device, launches);
+static zeta_status run_large_on(DeviceEngine *e, LgSlot &slot, Instance &X, std::string &err, double *ms_device,
+                                uint64_t *launches) {
+    if (X.q < ((uint64_t)1 << 26)) return run_large_impl<uint32_t, true>(e, slot, X, err, ms_device, launches);
+    return X.q < ((uint64_t)1 << 32) ? run_large_impl<uint32_t, false>(e, slot, X, err, ms_device, launches)
+                                     : run_large_impl<uint64_t, false>(e, slot, X, err, ms_device, launches);
+}
+
+// Lanes 0 .. n-1 of the whole-GPU executor (lane 0 on the engine's stream, the others on streams of their own).
+static zeta_status lg_lanes(DeviceEngine *e, size_t n, std::string &err) {
+    if (e->lg.empty()) {
+        e->lg.emplace_back();
+        e->lg[0].stream = e->stream;
+    }
+    while (e->lg.size() < n) {
+        LgSlot sl;
+        CUDA_TRY(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+        sl.owned = true;
+        e->lg.push_back(std::move(sl));
+    }
+    return ZETA_OK;
+}
+
+constexpr size_t kLgLanes = 8;
+
+zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::string &err, double *ms_device,
+                             uint64_t *launches) {
+    *ms_device = 0;
+    *launches = 0;
+    if (xs.empty()) return ZETA_OK;
+    CUDA_TRY(cudaSetDevice(e->device));
+    zeta_status st = upload_binom(e, err);
+    if (st) return st;
+    if ((st = lg_lanes(e, 1, err))) return st;
+    std::vector<Instance *> whole, shared;
+    for (Instance *X : xs) (X->s > 512 ? whole : shared).push_back(X);
+    // instances with s > 512 fill the GPU: one at a time on lane 0
+    for (Instance *X : whole) {
+        double ms = 0;
+        uint64_t nl = 0;
+        if ((st = run_large_on(e, e->lg[0], *X, err, &ms, &nl))) return st;
+        *ms_device += ms;
+        *launches += nl;
+    }
+    if (shared.empty()) return ZETA_OK;
+    // smaller ones (quintic surfaces: s = 455, about 10 000 short launches each) leave most SMs idle and are bound
+    // by launch latency: up to eight at a time, each lane driven by a host thread of its own
+    const size_t G = std::min(kLgLanes, shared.size());
+    if ((st = lg_lanes(e, G, err))) return st;
+    std::vector<zeta_status> sts(G, ZETA_OK);
+    std::vector<std::string> errs(G);
+    std::vector<uint64_t> nls(G, 0);
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<std::thread> pool;
+    for (size_t g = 0; g < G; g++)
+        pool.emplace_back([&, g]() {
+            if (cudaSetDevice(e->device) != cudaSuccess) {
+                sts[g] = ZETA_ERR_DEVICE;
+                errs[g] = "cudaSetDevice";
+                return;
+            }
+            for (size_t i = g; i < shared.size(); i += G) {
+                double ms = 0;
+                uint64_t nl = 0;
+                const zeta_status s2 = run_large_on(e, e->lg[g], *shared[i], errs[g], &ms, &nl);
+                if (s2) {
+                    sts[g] = s2;
+                    return;
+                }
+                nls[g] += nl;
+            }
+        });
+    for (auto &t : pool) t.join();
+    for (size_t g = 0; g < G; g++)
+        if (sts[g]) {
+            err = errs[g];
+            return sts[g];
+        }
+    *ms_device += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (uint64_t nl : nls) *launches += nl;
+    return ZETA_OK;
 }
 
 // ---------------------------------------------------------------------------
