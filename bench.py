@@ -320,6 +320,44 @@ def _mixed_stream(z, ctx, stream, torch):
             "busy_ms_median_by_class": {k: statistics.median(v) for k, v in sorted(by_class.items())}}
 
 
+def _mixed_stream_r1(z, ctx, stream, torch):
+    """A 64-instance stream at relative precision 1 with every size the library takes: the mixed stream's quartic
+    curve, 24 quintic curves, 16 cubic surfaces, the first 16 of its K3 surfaces and its 2 Fermat cubic threefolds in
+    one persistent launch, then 4 quintic surfaces (b = 52) and the Fermat cubic fourfold (s = 3003) on the whole-GPU
+    executor, all from one zeta_batch_run.  Latency per instance: device time inside the persistent launch (cluster
+    executor stamps) for the first 59, host time after the run call for the other 5."""
+    accept = _accept_r1(z)
+    ks = list(range(1 + 24 + 16 + 16)) + [len(zi.MIXED_STREAM) - 2, len(zi.MIXED_STREAM) - 1]
+    specs = [zi.draw_mixed(k, accept) for k in ks]
+    specs += [zi.draw_instance("quintic_surfaces", i, accept)[:4] for i in range(4)]
+    specs.append((5, 3, 7, zi.fermat(5, 3)))
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", r=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.run()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    P, per, tot = plan.finish()
+    plan.release()
+    lat = sorted(st["ms_dev_end"] for st in per)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * len(lat)))]
+    by_class = {}
+    for (n, d, p, c), st in zip(specs, per):
+        key = "n%d_d%d_s%d_b%d" % (n, d, st["s"], st["b"])
+        by_class.setdefault(key, []).append(st["ms_dev_end"])
+    return {"workload": "mixed_stream_64_r1", "composition": "1 quartic curve, 24 quintic curves, 16 cubic "
+            "surfaces, 16 quartic K3 surfaces, 2 Fermat cubic threefolds (persistent launch), 4 quintic surfaces "
+            "and the Fermat cubic fourfold (whole-GPU executor)", "precision": "relative precision r = 1",
+            "wall_s": wall, "zeta_per_s": len(specs) / wall,
+            "completed": "%d/%d" % (sum(1 for st in per if st["status"] == 0), len(specs)),
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "max": lat[-1],
+                           "meaning": "completion after the run call: device clock inside the persistent launch, "
+                                      "host clock on the whole-GPU executor"},
+            "completion_ms_median_by_class": {k: statistics.median(v) for k, v in sorted(by_class.items())}}
+
+
 def _accept_r1(z):
     def accept(n, d, p, c):
         try:
@@ -481,7 +519,7 @@ def main():
                     help="truncate the K3 line's series orders to N (small profiling case; 0 = full precision)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 64-instance mixed stream")
     ap.add_argument("--no-fourfold", action="store_true", help="skip the cubic fourfold line (Fermat, r = 1)")
-    ap.add_argument("--only", default=None, choices=["fourfold", "surfaces"],
+    ap.add_argument("--only", default=None, choices=["fourfold", "surfaces", "mixed_r1"],
                     help="run only this line (profiling a small case of its kernels) and print it")
     ap.add_argument("--fourfold-N", type=int, default=0,
                     help="series order override of the --only fourfold run (a small case; 0 = the rule)")
@@ -511,6 +549,10 @@ def main():
     if args.only == "fourfold":
         print(json.dumps({"cubic_fourfolds": _cubic_fourfolds(z, ctx, stream, torch, args.fourfold_dense,
                                                               args.fourfold_N)}))
+        z.zeta_destroy(ctx)
+        return
+    if args.only == "mixed_r1":
+        print(json.dumps({"mixed_stream_r1": _mixed_stream_r1(z, ctx, stream, torch)}))
         z.zeta_destroy(ctx)
         return
     if args.only == "surfaces":
@@ -710,6 +752,11 @@ def main():
             line["quintic_surfaces"] = _quintic_surfaces(z, ctx, stream, torch, args.surface_count, 24)
         except Exception as exc:   # reported, never a reason to lose the main line
             line["quintic_surfaces"] = {"error": repr(exc)[:200]}
+    if rank == 0 and world == 1 and not args.no_mixed:
+        try:
+            line["mixed_stream_r1"] = _mixed_stream_r1(z, ctx, stream, torch)
+        except Exception as exc:   # reported, never a reason to lose the main line
+            line["mixed_stream_r1"] = {"error": repr(exc)[:200]}
     if rank == 0 and world == 1 and not args.no_fourfold:
         try:
             line["cubic_fourfolds"] = _cubic_fourfolds(z, ctx, stream, torch, args.fourfold_dense)

@@ -164,7 +164,10 @@ typedef struct {
      * which its numerators were written back; the instance's result is
      * complete on the device at ms_dev_end.  Recorded by the cluster executor,
      * which runs every batch holding an instance with s > 128 (all of the
-     * batch's instances); batches of smaller instances report 0 for both. */
+     * batch's instances); batches of smaller instances report 0 for both.
+     * Instances on the whole-GPU executor (C(dn, n) > 512 or more than 32
+     * basis columns) report host-clock times after zeta_batch_run was called:
+     * their run's start and its completion. */
     double ms_dev_start;
     double ms_dev_end;
 } zeta_stats;

@@ -191,9 +191,10 @@ zeta_status engine_horner(DeviceEngine *e, zeta_path path, uint32_t count, uint3
 // sets done, ok (full row rank) and X.  Jobs too wide for the kernel's shared memory are left undone.
 // Runs the instances' plans on the whole-GPU executor (zeta_large.cuh) and fills their H (s <= 4096, b <= 64,
 // q < 2^56): s > 512 one at a time; smaller ones up to eight at a time on lanes of their own.  ms_device: CUDA-event
-// time of the former plus the elapsed time of the latter.
+// time of the former plus the elapsed time of the latter.  Each instance's start and completion go to
+// ms_dev_start / ms_dev_end as host-clock milliseconds after t_ref_ms (steady clock).
 zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::string &err, double *ms_device,
-                             uint64_t *launches);
+                             uint64_t *launches, double t_ref_ms);
 zeta_status engine_solve(DeviceEngine *e, const std::vector<SolveJob *> &jobs, const std::vector<uint64_t> &qs,
                          const std::vector<uint64_t> &ps, std::string &err, double *ms_device);
 

@@ -1539,6 +1539,10 @@ static zeta_status run_large_impl(DeviceEngine *e, LgSlot &slot, Instance &X, st
     uint64_t nl = 0;
     CUDA_TRY(cudaSetDevice(e->device));
     const int s = (int)X.s, b = (int)X.b, nv = (int)X.nv;
+    if (NARROW && (uint64_t)X.sec_rows * X.sec_cols >= ((uint64_t)1 << 32)) {
+        err = "whole-GPU executor: section of 2^32 words or more";
+        return ZETA_ERR_UNSUPPORTED;
+    }
     if (s < 1 || s > 4096 || b < 1 || b > 64 || X.q >= ((uint64_t)1 << 56) || X.sec.empty()) {
         err = "whole-GPU executor: needs s <= 4096, b <= 64, q < 2^56";
         return ZETA_ERR_UNSUPPORTED;
@@ -1630,7 +1634,7 @@ static zeta_status run_large_impl(DeviceEngine *e, LgSlot &slot, Instance &X, st
                 nl += 2;
                 k_lg_colidx<<<blocks_for((size_t)s, 256), 256, 0, stream>>>(s, nv, (int)X.kappa, d_monoS, v, d_colidx);
                 if constexpr (NARROW)
-                    k_lg_gen_narrow<<<blocks_for(ss, 256), 256, 0, stream>>>(
+                    k_lg_gen_narrow<<<dim3(blocks_for((size_t)sp, 256), (unsigned)s), 256, 0, stream>>>(
                         s, sp, nv, X.sec_cols, d_monoS, d_secrow, d_colidx, (const uint32_t *)d_sec, U, v, Q,
                         (uint32_t *)d_M, (uint32_t *)d_A);
                 else
@@ -1727,8 +1731,12 @@ static zeta_status lg_lanes(DeviceEngine *e, size_t n, std::string &err) {
 
 constexpr size_t kLgLanes = 8;
 
+static double steady_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::string &err, double *ms_device,
-                             uint64_t *launches) {
+                             uint64_t *launches, double t_ref_ms) {
     *ms_device = 0;
     *launches = 0;
     if (xs.empty()) return ZETA_OK;
@@ -1738,19 +1746,11 @@ zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::
     if ((st = lg_lanes(e, 1, err))) return st;
     std::vector<Instance *> whole, shared;
     for (Instance *X : xs) (X->s > 512 ? whole : shared).push_back(X);
-    // instances with s > 512 fill the GPU: one at a time on lane 0
-    for (Instance *X : whole) {
-        double ms = 0;
-        uint64_t nl = 0;
-        if ((st = run_large_on(e, e->lg[0], *X, err, &ms, &nl))) return st;
-        *ms_device += ms;
-        *launches += nl;
-    }
-    if (shared.empty()) return ZETA_OK;
-    // smaller ones (quintic surfaces: s = 455, about 10 000 short launches each) leave most SMs idle and are bound
-    // by launch latency: up to eight at a time, each lane driven by a host thread of its own
-    const size_t G = std::min(kLgLanes, shared.size());
-    if ((st = lg_lanes(e, G, err))) return st;
+    // smaller ones first (quintic surfaces: s = 455, about 10 000 short launches each), so that a stream's short
+    // instances do not wait for its cubic fourfold; they leave most SMs idle and are bound by launch latency: up to
+    // eight at a time, each lane driven by a host thread of its own
+    const size_t G = std::min(kLgLanes, shared.size());  // 0: no thread
+    if ((st = lg_lanes(e, std::max<size_t>(G, 1), err))) return st;
     std::vector<zeta_status> sts(G, ZETA_OK);
     std::vector<std::string> errs(G);
     std::vector<uint64_t> nls(G, 0);
@@ -1766,7 +1766,9 @@ zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::
             for (size_t i = g; i < shared.size(); i += G) {
                 double ms = 0;
                 uint64_t nl = 0;
+                shared[i]->ms_dev_start = steady_ms() - t_ref_ms;
                 const zeta_status s2 = run_large_on(e, e->lg[g], *shared[i], errs[g], &ms, &nl);
+                shared[i]->ms_dev_end = steady_ms() - t_ref_ms;
                 if (s2) {
                     sts[g] = s2;
                     return;
@@ -1780,8 +1782,19 @@ zeta_status engine_run_large(DeviceEngine *e, std::vector<Instance *> &xs, std::
             err = errs[g];
             return sts[g];
         }
-    *ms_device += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (!shared.empty())
+        *ms_device += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     for (uint64_t nl : nls) *launches += nl;
+    // then the instances with s > 512, which fill the GPU: one at a time on lane 0
+    for (Instance *X : whole) {
+        double ms = 0;
+        uint64_t nl = 0;
+        X->ms_dev_start = steady_ms() - t_ref_ms;
+        if ((st = run_large_on(e, e->lg[0], *X, err, &ms, &nl))) return st;
+        X->ms_dev_end = steady_ms() - t_ref_ms;
+        *ms_device += ms;
+        *launches += nl;
+    }
     return ZETA_OK;
 }
 

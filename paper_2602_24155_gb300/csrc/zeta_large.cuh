@@ -142,16 +142,18 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step(int s, int c, const u
 // below 2^52, so a 64-bit sum of up to 4096 of them needs no limbs -- one mad.wide.u32 per product.  M and A
 // are 32-bit words in rows of stride sp (s rounded up to 4, the padding zero), read 16 bytes at a time.
 
-// A R and M(k-1) R as above, from Sec R^2 mod q (32-bit words): each is one REDC of a sum below 2^48.
+// A R and M(k-1) R as above, from Sec R^2 mod q (32-bit words): each is one REDC of a sum below 2^48.  Grid:
+// (sp / 256 rounded up, s); block y is row r, threads run over j; every product is one mad.wide.u32 (a section word
+// below 2^26 times a weight below 2^16) and every index fits 32 bits (the section has under 2^32 words).
 __global__ void __launch_bounds__(256) k_lg_gen_narrow(int s, int sp, int nv, uint32_t sec_cols,
                                                        const int32_t *__restrict__ monoS,
                                                        const int32_t *__restrict__ secrow,
                                                        const int32_t *__restrict__ colidx,
                                                        const uint32_t *__restrict__ SecRR, LgVec U, LgVec v, ModQ Q,
                                                        uint32_t *__restrict__ M, uint32_t *__restrict__ A) {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (size_t)s * sp) return;
-    const int r = (int)(e / (size_t)sp), j = (int)(e % (size_t)sp);
+    const int r = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= sp) return;
     uint64_t aL = 0, mL = 0;
     const int col = j < s ? colidx[j] : -1;
     if (col >= 0) {
@@ -162,17 +164,18 @@ __global__ void __launch_bounds__(256) k_lg_gen_narrow(int s, int sp, int nv, ui
         for (int i = 0; i < kMaxVars; i++) {
             val[i] = 0;
             if (i < nv) {
-                const int row = secrow[i * s + r];
-                if (row >= 0) val[i] = __ldg(&SecRR[(size_t)row * sec_cols + col]);
+                const int row = __ldg(&secrow[i * s + r]);
+                if (row >= 0) val[i] = __ldg(&SecRR[(uint32_t)row * sec_cols + (uint32_t)col]);
             }
         }
 #pragma unroll
         for (int i = 0; i < kMaxVars; i++)
             if (i < nv) {
-                aL += (uint64_t)val[i] * (uint64_t)v.x[i];
-                mL += (uint64_t)val[i] * (uint64_t)(U.x[i] - v.x[i] + monoS[r * nv + i]);
+                madw(aL, val[i], (uint32_t)v.x[i]);
+                madw(mL, val[i], (uint32_t)(U.x[i] - v.x[i] + __ldg(&monoS[r * nv + i])));
             }
     }
+    const size_t e = (size_t)r * sp + j;
     A[e] = (uint32_t)redc(aL, 0, Q);
     M[e] = (uint32_t)redc(mL, 0, Q);
 }
@@ -209,7 +212,8 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp,
         }
         __syncthreads();
         if (row_ok) {
-#pragma unroll 2
+            // four 16-byte loads of M and A in flight per lane: the step is bound by memory latency otherwise
+#pragma unroll 4
             for (int q4 = lane; q4 < (jn >> 2); q4 += 32) {
                 const int g = (j0 >> 2) + q4;
                 const uint4 m = Mr[g];
