@@ -116,3 +116,27 @@ def test_first_slope_length_is_the_p_rank_for_curves_and_the_slope_one_length_fo
     for P in (ordinary, almost, lower):
         low = [a % p ** (1 + H[i]) for i, a in enumerate(P)]
         assert first_slope_length(low, p, 1) == first_slope_length(P, p, 1)
+
+
+def test_fourfold_height_rule_and_hodge_polygon():
+    """Cubic fourfolds: H(i) = 2i - 1 on 1..21 and 44 at 22 (Hodge numbers 1, 20, 1); the height is the least i with
+    v(a_i) <= 2i - 1, decided by a_i mod p^(2i).  Synthetic polygons of heights 1, 2, 3 and a supersingular one, the
+    Fermat cubic fourfold over F_7 (ordinary: p = 1 mod 3) from Weil's Gauss-sum formula, and the dense fourfold of
+    tests/golden/cubic_fourfold_f7.txt whose a_1 = 0 and a_2 = -7^4 (point counts) rule out heights 1 and 2."""
+    from oracle import pins
+    from paper_2602_24155_gb300.newton import fourfold_height, hodge_polygon
+    H = hodge_polygon(5, 3)
+    assert H[:4] == [0, 1, 3, 5] and H[21] == 41 and H[22] == 44 and len(H) == 23
+    assert hodge_polygon(3, 5)[4] == 0 and hodge_polygon(3, 5)[5] == 1 and hodge_polygon(3, 5)[52] == 52
+    p = 7
+    base = [1] + [p ** (2 * i) for i in range(1, 23)]    # every a_i of valuation 2i: no finite height <= 11
+    h1 = list(base); h1[1] = 3 * p
+    h2 = list(base); h2[2] = 5 * p ** 3
+    h3 = list(base); h3[3] = 2 * p ** 5
+    assert [fourfold_height(P, p) for P in (h1, h2, h3)] == [1, 2, 3]
+    assert fourfold_height(base, p) is None
+    assert fourfold_height(pins.fermat_charpoly(5, 3, 7), 7) == 1
+    s1, s2 = 2801 - sum(p ** i for i in range(5)), 5889703 - sum(p ** (2 * i) for i in range(5))
+    a1, a2 = -s1, (s1 * s1 - s2) // 2
+    assert a1 == 0 and a2 == -p ** 4
+    assert fourfold_height([1, a1, a2] + [0] * 20, p) != 1 and fourfold_height([1, a1, a2] + [0] * 20, p) != 2
