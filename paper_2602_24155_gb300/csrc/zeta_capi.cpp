@@ -81,6 +81,8 @@ static void fill_stats(const Instance &X, zeta_stats *st, double ms_device) {
     st->ms_dev_end = X.ms_dev_end;
 }
 
+static uint64_t step_side(uint32_t n, uint32_t d);
+
 static zeta_options default_options() {
     zeta_options o;
     std::memset(&o, 0, sizeof(o));
@@ -136,14 +138,34 @@ zeta_status zeta_query(const zeta_hypersurface *hs, const zeta_options *opt, uin
 static zeta_status run_one(zeta_ctx *ctx, const zeta_hypersurface *hs, const zeta_options *opt, Instance &X,
                            double *ms_dev) {
     zeta_options o = opt ? *opt : default_options();
-    zeta_status st = prepare_instance(hs, &o, true, X);
+    // C(dn, n) > 512: the setup's right inverses on the device (the host refuses them)
+    const bool big = hs && step_side(hs->n, hs->d) > 512;
+    zeta_status st = prepare_instance(hs, &o, true, X, big);
     X.net.w = o.policy_weights;
     X.net.hidden = (int)o.policy_hidden;
+    if (!st && X.solves_pending) {
+        std::vector<SolveJob *> jobs;
+        std::vector<uint64_t> qs, ps;
+        for (SolveJob &J : X.solves)
+            if (J.R) {
+                jobs.push_back(&J);
+                qs.push_back(X.q);
+                ps.push_back(X.p);
+            }
+        st = engine_solve(ctx->engine, jobs, qs, ps, ctx->error, nullptr);
+        if (st) return st;
+        st = prepare_complete(X);
+    }
     if (!st) st = schedule_policy(X, o.policy);
     if (st) { ctx->error = X.error; return st; }
     std::vector<Instance *> batch{&X};
-    resolve_path(ctx, batch, o);
-    st = engine_run(ctx->engine, batch, o.policy, o.path, o.block_threads, ctx->error, ms_dev);
+    if (X.s > 512 || X.b > 32 || (o.flags & ZETA_FLAG_WHOLE_GPU)) {
+        uint64_t launches = 0;
+        st = engine_run_large(ctx->engine, batch, ctx->error, ms_dev, &launches, now_ms());
+    } else {
+        resolve_path(ctx, batch, o);
+        st = engine_run(ctx->engine, batch, o.policy, o.path, o.block_threads, ctx->error, ms_dev);
+    }
     if (st) return st;
     st = (o.flags & ZETA_FLAG_Y_ONLY) ? finish_y_only(X) : finish_instance(X);
     if (st) { ctx->error = X.error; return st; }

@@ -1,6 +1,6 @@
 """Writes the stored expected values under tests/golden/ from the oracle alone.
 
-Run from the repository root:  python tests/golden/make_golden.py [k3 | threefold | fourfold]
+Run from the repository root:  python tests/golden/make_golden.py [k3 | threefold | fourfold | surface]
 Each value is produced by oracle/ (which the point-count and closed-form
 tests pin); nothing here touches the CUDA path.  `k3` writes the
 full-precision P(T) of three quartic K3 surfaces (tens of minutes of CPU per
@@ -9,7 +9,9 @@ threefold over F_11 drawn with seed 11 (S = {4}) at series order N = 6, the
 least N whose columns reach the relative precision r = (5, 6) (about half an
 hour of CPU).  `fourfold` writes #X(F_7) and #X(F_49) of a dense cubic
 fourfold (point counts, about ten minutes of CPU): its P(T) is beyond the
-oracle's reach (s = 3003), the counts fix a_1 and a_2.
+oracle's reach (s = 3003), the counts fix a_1 and a_2.  `surface` writes the
+unnormalised Frobenius columns Y of quintic surfaces at relative precision 1
+(b = 52, Y mod 7^3; about a minute of CPU each).
 """
 import multiprocessing as mp
 import os
@@ -107,6 +109,26 @@ def fourfold_main():
         fh.write("counts: %s\n" % " ".join(map(str, counts)))
 
 
+def surface_main():
+    """Y (52 x 52, mod q = p^M, unnormalised) of quintic surfaces at relative precision r = 1: the Fermat quintic
+    surface over F_7 and the first dense surface of the quintic_surfaces workload."""
+    n, d, p = 3, 5, 7
+    cases = [("fermat", zi.fermat(n, d)),
+             ("quintic_surfaces_0", zi.draw_instance("quintic_surfaces", 0, cohomology.is_smooth)[3])]
+    with open(os.path.join(HERE, "quintic_surfaces_r1.txt"), "w") as fh:
+        fh.write("# quintic surfaces over F_7 at relative precision r = 1: Y = unnormalised Frobenius columns\n")
+        fh.write("# (b x b, row-major, mod q), the same for every policy and every S\n")
+        for name, c in cases:
+            t = time.time()
+            res = zeta.compute_zeta(n, d, p, c, r=1, normalise=False, want_P=False)
+            fh.write("case: %s\n" % name)
+            fh.write("n d p: %d %d %d\n" % (n, d, p))
+            fh.write("coeffs: %s\n" % " ".join(map(str, c)))
+            fh.write("q: %d\n" % res.prec.q)
+            fh.write("oracle seconds: %.0f\n" % (time.time() - t))
+            fh.write("Y: %s\n" % " ".join(str(int(v)) for v in res.Y.reshape(-1)))
+
+
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "k3":
         k3_main()
@@ -114,5 +136,7 @@ if __name__ == "__main__":
         threefold_main()
     elif len(sys.argv) > 1 and sys.argv[1] == "fourfold":
         fourfold_main()
+    elif len(sys.argv) > 1 and sys.argv[1] == "surface":
+        surface_main()
     else:
         main()

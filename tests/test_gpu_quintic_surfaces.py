@@ -71,3 +71,36 @@ def test_dense_quintic_surfaces_equal_hasse_witt(ctx):
         want = [(hw[t] if t < len(hw) else 0) % p for t in range(53)]
         for policy in out:
             assert out[policy][i] == want, (i, policy)
+
+
+def _surface_golden():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "quintic_surfaces_r1.txt")
+    cases, cur = [], None
+    for line in open(path):
+        if line.startswith("#") or ":" not in line:
+            continue
+        key, _, val = line.partition(":")
+        key, val = key.strip(), val.strip()
+        if key == "case":
+            cur = {"name": val}
+            cases.append(cur)
+        else:
+            cur[key] = val
+    return cases
+
+
+def test_quintic_surface_Y_equals_the_oracle(ctx):
+    """The unnormalised Frobenius columns Y (52 x 52 mod 7^3) of the Fermat quintic surface and a dense one over F_7
+    at relative precision 1, through the single-instance call on the whole-GPU executor, equal the oracle's
+    (tests/golden/quintic_surfaces_r1.txt, written by make_golden.py surface from the oracle alone), for two
+    policies (Y depends on neither the policy nor S)."""
+    import numpy as np
+    for case in _surface_golden():
+        n, d, p = map(int, case["n d p"].split())
+        c = [int(x) for x in case["coeffs"].split()]
+        want = np.array([int(x) for x in case["Y"].split()], dtype=object).reshape(52, 52)
+        for policy in ("p_chunk", "cover"):
+            F, Y, st = z.zeta_frobenius(ctx, (n, d, p, c), r=1, y_only=True, policy=policy)
+            assert st["b"] == 52 and st["s"] == 455
+            assert (Y.astype(object) == want).all(), (case["name"], policy)
