@@ -99,3 +99,25 @@ def test_every_run_of_a_prepared_batch_launches_again(ctx):
     plan.release()
     assert P1 == P3
     assert tot3["kernel_launches"] > tot1["kernel_launches"] and tot3["ms_kernel"] > tot1["ms_kernel"]
+
+
+def test_pipelined_batch_with_device_setup_equals_one_plan(ctx):
+    """zeta_batch on 256 instances or more splits them into sub-batches; when one holds an instance with s > 128 the
+    setup's right inverses of all sub-batches are solved on the device before the first launch.  256 quartic K3
+    surfaces at relative precision 1 through that path give the same P(T) and statuses as one prepared plan."""
+    def accept(n, d, p, c):
+        try:
+            z.zeta_query((n, d, p, c), r=1)
+            return True
+        except z.ZetaError as e:
+            if e.status == 2:
+                return False
+            raise
+    specs = [zi.draw_instance("quartic_k3", i, accept)[:4] for i in range(256)]
+    P1, per1, _ = z.zeta_batch(ctx, specs, policy="p_chunk", r=1)
+    plan = z.zeta_batch_prepare(ctx, specs, policy="p_chunk", r=1)
+    plan.run()
+    P2, per2, _ = plan.finish()
+    plan.release()
+    assert [st["status"] for st in per1] == [st["status"] for st in per2] == [0] * 256
+    assert P1 == P2
