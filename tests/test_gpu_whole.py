@@ -121,3 +121,14 @@ def test_pipelined_batch_with_device_setup_equals_one_plan(ctx):
     plan.release()
     assert [st["status"] for st in per1] == [st["status"] for st in per2] == [0] * 256
     assert P1 == P2
+
+
+def test_single_instance_call_on_a_cubic_fourfold(ctx):
+    """zeta_frobenius on an instance with C(dn, n) > 512 solves its right inverses on the device and runs it on the
+    whole-GPU executor: the Fermat cubic fourfold at series order 2 (a short plan; the columns Y are a truncation)
+    gives the same Y under two policies, as Y depends on neither."""
+    spec = (5, 3, 7, zi.fermat(5, 3))
+    F1, Y1, st1 = z.zeta_frobenius(ctx, spec, r=1, N=2, y_only=True, policy="p_chunk")
+    F2, Y2, st2 = z.zeta_frobenius(ctx, spec, r=1, N=2, y_only=True, policy="depth_first")
+    assert st1["s"] == 3003 and st1["b"] == 22 and st1["column_steps"] != st2["column_steps"]
+    assert (Y1 == Y2).all() and Y1.any()
