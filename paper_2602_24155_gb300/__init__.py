@@ -399,16 +399,27 @@ def zeta_plan(spec, **opt):
                           merges=info.plan_merges, entries=info.plan_entries, cap=info.plan_cap))
 
 
+def plan_sizes(spec, **opt):
+    """(b, sec_rows, sec_cols, h_rows) of zeta_plan's outputs, from n, d, S and zeta_query alone (no setup):
+    the section has (n+1) C(kappa-d+1+n, n) rows and C(kappa+n, n) columns, kappa = (n+1)(d-1)+1-|S|, and the
+    final map C(dn-1, n) columns."""
+    from math import comb
+    n, d, _, _ = spec
+    S = opt.get("S")
+    size_S = len(set(S)) if S else (n + 1 if d >= n + 1 else 1)
+    kappa = (n + 1) * (d - 1) + 1 - size_S
+    b = zeta_query(spec, **opt)[0]
+    return b, (n + 1) * comb(kappa - d + 1 + n, n), comb(kappa + n, n), comb(d * n - 1, n)
+
+
 def zeta_plan_device(ctx, spec, **opt):
-    """zeta_plan's section and final reduction map with the right inverses solved on the device.
-    Returns (sec, fin, kernel ms)."""
+    """zeta_plan's section and final reduction map with the right inverses solved on the device (any C(dn, n) up to
+    4096).  Returns (sec, fin, kernel ms)."""
     hs = _hypersurface(spec)
     o = _options(**opt)
-    info = PlanInfo()
-    _check(None, LIB.zeta_plan(ctypes.byref(hs), ctypes.byref(o), ctypes.byref(info), None, None, None,
-                               None, None, None))
-    sec = np.zeros((info.sec_rows, info.sec_cols), dtype=np.uint64)
-    fin = np.zeros((info.b, info.h_rows), dtype=np.uint64)
+    b, rows, cols, h_rows = plan_sizes(spec, **opt)
+    sec = np.zeros((rows, cols), dtype=np.uint64)
+    fin = np.zeros((b, h_rows), dtype=np.uint64)
     ms = ctypes.c_double(0)
     _check(ctx, LIB.zeta_plan_device(ctx, ctypes.byref(hs), ctypes.byref(o), sec.ctypes.data, fin.ctypes.data,
                                      ctypes.byref(ms)))

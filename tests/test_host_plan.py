@@ -505,3 +505,16 @@ def test_quintic_surface_plans_with_52_columns():
     with pytest.raises(z.ZetaError) as e:
         z.zeta_plan_moves(spec, r=1, policy="p_chunk")
     assert e.value.status == 3
+
+
+def test_plan_sizes_match_the_setup():
+    """The output sizes the device-setup binding allocates without running the setup equal zeta_plan's: plane
+    quartics and quintics, a cubic surface (S = {3}), a quartic K3 and S chosen by the caller."""
+    cases = [((2, 4, 11, zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)[3]), {}),
+             ((2, 5, 13, zi.draw_instance("quintic_curves", 2, cohomology.is_smooth)[3]), {}),
+             ((3, 3, 7, _cubic_surface(7)[3]), {}),
+             ((3, 4, 7, zi.fermat(3, 4)), {}),
+             ((2, 4, 11, zi.draw_instance("quartic_curve_f11", 0, cohomology.is_smooth)[3]), {"S": (1, 2)})]
+    for spec, opt in cases:
+        P = z.zeta_plan(spec, policy="p_chunk", **opt)
+        assert z.plan_sizes(spec, **opt) == (P["b"], P["sec"].shape[0], P["sec"].shape[1], P["fin"].shape[1])
