@@ -74,6 +74,7 @@ def test_device_right_inverses_dense_cubic_threefold(ctx):
           % (t_host, t_dev, ms))
     assert sec.shape == (2475, 1001)
     assert np.array_equal(sec, host["sec"]) and np.array_equal(fin, host["fin"])
+    assert _section_identity_ok(spec, sec, host["kappa"], host["q"], [0, 500, 1000])
 
 
 def test_batches_agree_with_host_and_device_setup(ctx):
@@ -91,3 +92,66 @@ def test_batches_agree_with_host_and_device_setup(ctx):
     for a, b, st in zip(out["host"][0], out["device"][0], out["device"][1]):
         if st == 0:
             assert a == b
+
+
+def _monos(nv, D):
+    out = []
+    def rec(pos, rem, cur):
+        if pos == nv - 1:
+            out.append(tuple(cur + [rem]))
+            return
+        for t in range(rem, -1, -1):
+            rec(pos + 1, rem - t, cur + [t])
+    if D >= 0:
+        rec(0, D, [])
+    return out
+
+
+def _section_identity_ok(spec, sec, kappa, q, cols):
+    """For each sampled column gamma of the section: sum_i G_i d_i f = x^gamma mod q, G_i from the rows (i, nu)."""
+    n, d, p, c = spec
+    nv = n + 1
+    md = _monos(nv, d)
+    f = {m: cf for m, cf in zip(md, c) if cf}
+    df = []
+    for i in range(nv):
+        g = {}
+        for m, cf in f.items():
+            if m[i]:
+                e = list(m); e[i] -= 1
+                g[tuple(e)] = (g.get(tuple(e), 0) + cf * m[i]) % q
+        df.append(g)
+    src = _monos(nv, kappa - d + 1)
+    rows = _monos(nv, kappa)
+    for gcol in cols:
+        acc = {}
+        for i in range(nv):
+            for a, nu in enumerate(src):
+                v = int(sec[i * len(src) + a, gcol])
+                if not v:
+                    continue
+                for m, cf in df[i].items():
+                    e = tuple(x + y for x, y in zip(nu, m))
+                    acc[e] = (acc.get(e, 0) + v * cf) % q
+        want = rows[gcol]
+        for e, v in acc.items():
+            if v != (1 if e == want else 0):
+                return False
+        if acc.get(want, 0) != 1:
+            return False
+    return True
+
+
+def test_device_right_inverses_dense_cubic_fourfold(ctx):
+    """The dense cubic fourfold of tests/golden/cubic_fourfold_f7.txt (C(15, 5) = 3003; the host refuses its setup):
+    its section (18 018 x 6188 over Z/7^9, from a 6188 x 24 206 elimination) and final map from the device, with
+    A x Sec = I checked on sampled columns of the section (the map of J_S applied to column gamma gives x^gamma)."""
+    c = zi.dense_candidate(5, 3, 7, 5, 76, 0)
+    spec = (5, 3, 7, c)
+    t0 = time.time()
+    sec, fin, ms = z.zeta_plan_device(ctx, spec, policy="p_chunk", r=1)
+    print("dense cubic fourfold: section %s and final map %s in %.1f s, solve kernels %.0f ms"
+          % (sec.shape, fin.shape, time.time() - t0, ms))
+    assert sec.shape == (6 * 3003, 6188) and fin.shape == (22, 2002)
+    assert sec.any() and fin.any()
+    assert _section_identity_ok(spec, sec, 12, 7 ** 9, [0, 3001, 6187])
