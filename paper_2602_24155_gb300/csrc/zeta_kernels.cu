@@ -1587,7 +1587,7 @@ static zeta_status run_large_impl(DeviceEngine *e, LgSlot &slot, Instance &X, st
     CUDA_TRY(cudaEventCreate(&ev[1]));
     CUDA_TRY(cudaEventRecord(ev[0], stream));
     auto blocks_for = [](size_t n, int t) { return (unsigned)((n + t - 1) / t); };
-    const unsigned step_grid = blocks_for((size_t)s, kLgWarps);
+    const unsigned step_grid = blocks_for((size_t)s, NARROW ? kLgWarps / kLgSplit : kLgWarps);
     const int hdeg = (int)(X.d * X.n - X.n - 1);
     const Plan &P = X.plan;
     cudaError_t le = cudaSuccess;

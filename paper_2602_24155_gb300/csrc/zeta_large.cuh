@@ -180,14 +180,15 @@ __global__ void __launch_bounds__(256) k_lg_gen_narrow(int s, int sp, int nv, ui
     M[e] = (uint32_t)redc(mL, 0, Q);
 }
 
-// Step t of a chunk for columns [0, c) (c <= CPT).  One warp per row, each lane four consecutive j per 16-byte
-// load; W staged in shared memory as 32-bit words, kLgTileJ columns j at a time.  W, V: 64-bit words, column
-// stride sp.  Two forms:
+// Step t of a chunk for columns [0, c) (c <= CPT).  kLgSplit warps per row, each lane four consecutive j per
+// 16-byte load, the warps' residues added through shared memory; W staged in shared memory as 32-bit words,
+// kLgTileJ columns j at a time.  W, V: 64-bit words, column stride sp.  Two forms:
 //  WRITE = false: V = M(k-1) W - t (A W), tR = t R mod q; M is only read (two products per entry: chunks with one
 //                 or two columns, where the step is bound by reading M and A);
 //  WRITE = true:  V = M W with the current M(k-1-t), and, when `last`, M <- M - A (one product per entry: chunks
 //                 with three or more columns, where the products dominate).
 constexpr int kLgTileJ = 1024;
+constexpr int kLgSplit = 2;  // warps per row of the narrow step (a row of 3003 words per warp leaves 20 warps per SM)
 
 template <int CPT, bool WRITE>
 __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp, int c, const uint64_t *__restrict__ W,
@@ -195,8 +196,9 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp,
                                                                   const uint32_t *__restrict__ A, ModQ Q, uint64_t tR,
                                                                   int last) {
     __shared__ __align__(16) uint32_t sW[CPT][kLgTileJ];
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kLgWarps + (threadIdx.x >> 5);
+    __shared__ uint64_t s_part[kLgWarps][CPT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * (kLgWarps / kLgSplit) + warp / kLgSplit, part = warp % kLgSplit;
     const bool row_ok = r < s;  // a warp past the last row still helps stage W
     uint64_t SM[CPT], SA[CPT];
 #pragma unroll
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp,
         if (row_ok) {
             // four 16-byte loads of M and A in flight per lane: the step is bound by memory latency otherwise
 #pragma unroll 4
-            for (int q4 = lane; q4 < (jn >> 2); q4 += 32) {
+            for (int q4 = lane + 32 * part; q4 < (jn >> 2); q4 += 32 * kLgSplit) {
                 const int g = (j0 >> 2) + q4;
                 const uint4 m = Mr[g];
                 uint4 a = make_uint4(0, 0, 0, 0);
@@ -241,7 +243,6 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp,
             }
         }
     }
-    if (!row_ok) return;
 #pragma unroll
     for (int t = 0; t < CPT; t++) {
         if (t >= c) break;
@@ -252,8 +253,14 @@ __global__ void __launch_bounds__(kLgWarps * 32) k_lg_step_narrow(int s, int sp,
         }
 #pragma unroll
         for (int off = 16; off; off >>= 1) z = addmod(z, __shfl_xor_sync(0xffffffffu, z, off), Q.q);
-        if (lane == 0) V[(size_t)t * sp + r] = z;
+        if (lane == 0) s_part[warp][t] = z;
     }
+    __syncthreads();  // the row's other warps have written their part
+    if (!row_ok || part != 0 || lane >= c) return;
+    uint64_t z = s_part[warp][lane];
+#pragma unroll
+    for (int k = 1; k < kLgSplit; k++) z = addmod(z, s_part[warp + k][lane], Q.q);
+    V[(size_t)lane * sp + r] = z;
 }
 
 // W = the live columns of the arrival block (or 0 without one).
